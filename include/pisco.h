@@ -1,0 +1,191 @@
+/*
+ * pisco.h -- C ABI of the GB300 pixel-space convolver (PISCO, arXiv:1908.05662).
+ *
+ * One TOD sample is the pixelised convolution of Sec. 4.2
+ * (eq. discrete_beam_conv_tensor):
+ *
+ *   d(theta0, phi0, psi0) = (s/2) (Omega_pix / Omega~) sum_k [ (1+eps) row_T(k) + (1-eps) row_Q(k) ]
+ *   row_T = B_TT I' + B_QT Q' + B_UT U',   row_Q = B_TQ I' + B_QQ Q' + B_UQ U',
+ *   (I', Q', U') = Lambda(-chi_k) (I_k, Q_k, U_k)       (eq. lambda_operator)
+ *
+ * over the HEALPix RING pixels k whose centre lies within `radius` of the
+ * pointing (k . p0 >= cos radius), with the beamsor elements re-pixelised
+ * bilinearly at the pixel's antenna coordinates (Sec. 2, Appendix A) and
+ * chi_k the Ludwig-3 co-polarisation angle (Appendix A).  D Lambda(chi) =
+ * (s/2)[(1+eps), (1-eps), 0, 0] (eq. M_pol), so only six beamsor elements
+ * enter; the library folds them into three maps per detector at plan time.
+ *
+ * Conventions shared by every call:
+ *  - Pointers are plain device pointers unless a parameter says "host".
+ *    The caller owns every pointer it passes; the plan copies sky and beams
+ *    at creation, so the caller may free them afterwards.  Outputs are
+ *    caller-allocated.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Device work
+ *    is stream-ordered and asynchronous; calls return after enqueueing.
+ *    Calls that share one plan must be ordered on one stream (they share the
+ *    plan's read-only tables only, but pisco_convolve_host also uses
+ *    plan-owned staging buffers).
+ *  - Argument errors are detected before any launch and return
+ *    PISCO_EINVAL with a message in pisco_last_error().  CUDA errors return
+ *    PISCO_ECUDA.
+ *  - Pointing angles are float64 radians: theta (colatitude) in [0, pi],
+ *    phi any finite value, psi any finite value.  A sample whose angles are
+ *    non-finite or whose theta lies outside [0, pi] produces NaN (and -1 in
+ *    pisco_disc_count) without touching memory for it.
+ *  - Sky maps: [3][12 nside^2], rows I, Q, U in RING order, contiguous.
+ *  - Beam grids: [n_det][6][grid_n][grid_n] float32, maps ordered
+ *    TT, QT, UT, TQ, QQ, UQ (element B_XY: X = input Stokes column,
+ *    Y = output row of eq. beamsor).  Element [j][i] is the beamsor at
+ *    tangent-plane coordinates u_i = sin(R)(2i/(grid_n-1) - 1) along theta'0
+ *    and v_j (same formula) along phi'0 (orthographic coordinates
+ *    u = k . theta'0, v = k . phi'0; eq. antenna_base_vectors).
+ */
+#ifndef PISCO_H
+#define PISCO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum pisco_status {
+    PISCO_OK = 0,
+    PISCO_EINVAL = 1,        /* bad argument; nothing was enqueued */
+    PISCO_ENOMEM = 2,        /* device or host allocation failed */
+    PISCO_ECUDA = 3,         /* a CUDA runtime call failed */
+    PISCO_ETIMEOUT = 4,      /* reserved: a bounded device wait gave up */
+    PISCO_EUNSUPPORTED = 5,  /* valid request this build does not implement */
+    PISCO_EDEVICE = 6        /* a kernel recorded an invariant violation */
+} pisco_status;
+
+/* Arithmetic of a plan (pisco_options.precision). */
+enum {
+    PISCO_FP64_PLAIN = 0, /* FP64 throughout, one CTA per sample: the plain reference path */
+    PISCO_FP32 = 1        /* FP32 arithmetic, FP64 only where offsets would cancel */
+};
+
+/* Element type of caller arrays (sky_dtype). */
+enum { PISCO_DTYPE_F32 = 0, PISCO_DTYPE_F64 = 1 };
+
+/* One detector (Sec. 3 eq. copol_bolo, Sec. 4.1 eq. M_pol): polarisation
+ * angle zeta (radians) from theta'0, polarisation efficiency 1 - eps,
+ * responsivity s. */
+typedef struct pisco_detector {
+    double zeta;
+    double eps;
+    double s_resp;
+} pisco_detector;
+
+typedef struct pisco_options {
+    int precision;     /* PISCO_FP64_PLAIN or PISCO_FP32 */
+    int tile_samples;  /* FP32 path: consecutive samples sharing one disc traversal: 8, 16 or 32 (0 = 16) */
+    int reserved0;
+    int reserved1;
+} pisco_options;
+
+typedef struct pisco_plan pisco_plan;  /* opaque, owned by the library */
+
+/*
+ * pisco_plan_create -- build the device tables for one sky and n_det beams.
+ *
+ * Sec. 5.1: PISCO receives the sky maps, the beamsor and the focal plane
+ * (zeta per detector); Sec. 5.2's beam interpolation grid is assembled here.
+ *   nside        HEALPix resolution, 1 <= nside <= 8192.
+ *   radius_rad   disc cut-off rho_max (Sec. 5.3, Table 1) = beam grid radius,
+ *                0 < radius < pi/2.
+ *   sky          device, [3][12 nside^2] of sky_dtype (I, Q, U; V is zero, Sec. 6.2).
+ *   n_det, dets  host array of n_det >= 1 detectors.
+ *   grid_n       nodes per grid side, 2 <= grid_n <= 4096.
+ *   beam_grids   device float32 [n_det][6][grid_n][grid_n].
+ *   omega_tilde  host [n_det] normalisations Omega~ = int B_TT dOmega (Sec. 3), or
+ *                NULL to compute each from B_TT by the trapezoid rule over the
+ *                grid with area element du dv / sqrt(1 - u^2 - v^2).
+ *   opt          NULL for defaults (PISCO_FP32, 16 samples per tile).
+ *   stream       stream for the set-up kernels; the call synchronises it once.
+ * On success *out holds a new plan.  On failure *out is NULL and
+ * pisco_last_error(NULL) describes the error.
+ */
+pisco_status pisco_plan_create(pisco_plan** out, int nside, double radius_rad,
+                               const void* sky, int sky_dtype,
+                               int n_det, const pisco_detector* dets,
+                               int grid_n, const float* beam_grids,
+                               const double* omega_tilde,
+                               const pisco_options* opt, void* stream);
+
+/* Free a plan and its device memory (synchronises the device first).  NULL is a no-op. */
+void pisco_plan_destroy(pisco_plan* plan);
+
+/* Message of the last error on `plan`, or of the last failed create when plan is NULL. */
+const char* pisco_last_error(const pisco_plan* plan);
+
+/* Host copy of Omega~ and of the TOD scale (s/2) Omega_pix / Omega~ of detector det. */
+pisco_status pisco_plan_omega(const pisco_plan* plan, int det, double* omega_tilde, double* scale);
+
+/*
+ * pisco_convolve -- TOD of detector `det` for n pointings (Sec. 4.2, eq.
+ * discrete_beam_conv_tensor; Sec. 5.2's per-pointing loop L1 over the disc loop L2).
+ *   theta, phi, psi  device float64 [n].
+ *   tod              device [n]: float32 for a PISCO_FP32 plan, float64 for
+ *                    PISCO_FP64_PLAIN; overwritten.
+ * n = 0 is a valid no-op.  Long scans may be split into consecutive calls on
+ * sub-ranges (pointer offsets); results do not depend on the split.
+ */
+pisco_status pisco_convolve(pisco_plan* plan, int det, int64_t n,
+                            const double* theta, const double* phi, const double* psi,
+                            void* tod, void* stream);
+
+/*
+ * pisco_convolve_batched -- a focal plane in one launch (Sec. 5.1: several
+ * detectors in one pointing stream).  Detector d (0 <= d < n_det <= plan's
+ * n_det) owns samples offsets[d] .. offsets[d+1]-1 of the concatenated
+ * arrays; offsets is a host array of n_det + 1 non-decreasing values with
+ * offsets[0] = 0.  tod is concatenated the same way.  Plain plans run one
+ * launch per detector.
+ */
+pisco_status pisco_convolve_batched(pisco_plan* plan, int n_det, const int64_t* offsets,
+                                    const double* theta, const double* phi, const double* psi,
+                                    void* tod, void* stream);
+
+/*
+ * pisco_adjoint -- transpose of pisco_convolve with respect to the sky:
+ * maps[m][k] (+)= sum_t tod[t] * d d_t / d S^m_k for m = I, Q, U.
+ *   tod    device [n], float32 (FP32 plan) or float64 (plain plan).
+ *   maps   device [3][12 nside^2] of the same type; zeroed first unless
+ *          accumulate != 0.  Uses atomic adds: the summation order, hence
+ *          the last bits, vary from run to run.
+ */
+pisco_status pisco_adjoint(pisco_plan* plan, int det, int64_t n,
+                           const double* theta, const double* phi, const double* psi,
+                           const void* tod, void* maps, int accumulate, void* stream);
+
+/*
+ * pisco_disc_count -- number of sky pixels in the disc of each pointing
+ * (the pixel list of Sec. 5.2, cut at rho_max as in Table 1), decided by
+ * the plan's own path (the FP32 path filters in FP32 and settles pixels
+ * within 2e-6 of the boundary in FP64).  counts: device int32 [n]; -1 for
+ * an invalid sample.
+ */
+pisco_status pisco_disc_count(pisco_plan* plan, int64_t n, const double* theta,
+                              const double* phi, int32_t* counts, void* stream);
+
+/*
+ * pisco_convolve_host -- pisco_convolve with HOST buffers: copies the
+ * pointing to the device in chunks, convolves and copies the TOD back,
+ * overlapping the copies of one chunk with the kernel of the previous one
+ * on two internal streams.  Synchronous: returns when h_tod is written.
+ * Pinned host memory gives asynchronous copies; pageable memory works.
+ */
+pisco_status pisco_convolve_host(pisco_plan* plan, int det, int64_t n,
+                                 const double* h_theta, const double* h_phi,
+                                 const double* h_psi, void* h_tod);
+
+/* Synchronise the plan's work on `stream` and report any error a kernel
+ * recorded since the last call (PISCO_EDEVICE), clearing it. */
+pisco_status pisco_sync_status(pisco_plan* plan, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PISCO_H */

@@ -1,0 +1,418 @@
+// FP32 tile kernel: TOD (forward), sky transpose (adjoint) and disc counts.
+//
+// One CTA owns a tile of S consecutive samples of one detector (Sec. 5.2 gives
+// one block per pointing; consecutive samples of a scan share almost all of
+// their disc, so here one disc traversal serves S pointings).  Per tile:
+//
+//  1. per sample, in FP64: the antenna basis (eq. antenna_base_vectors),
+//     rounded to FP32 constants;
+//  2. samples are grouped greedily into runs whose pointings lie within
+//     R/4 of the run's first one and within R/2 in longitude; each run
+//     shares one traversal of the union of its discs (the ring-ordered
+//     disc query of Sec. 5.2, done on the device);
+//  3. per (ring, sample), FP64 -> FP32: sin(theta_r - theta0) and
+//     1 - cos(theta_r - theta0), so the in-frame offsets of every pixel are
+//     formed from small, well-conditioned terms:
+//        x0 = k . theta0_hat = sin(dtheta) - 2 cos(theta0) sin(theta_r) sin^2(dphi/2)
+//        y0 = k . phi0_hat   = 2 sin(theta_r) sin(dphi/2) cos(dphi/2)
+//        1 - k . p0          = (1 - cos dtheta) + 2 sin(theta0) sin(theta_r) sin^2(dphi/2)
+//     with dphi/2 rotated from per-pixel and per-sample half-angles, and
+//     (x, y) = (x0, y0) rotated by psi0 (Sec. 2): no O(1) terms cancel in FP32;
+//  4. disc membership 1 - k . p0 <= 1 - cos R is decided in FP32; pairs
+//     within 2e-6 (relative) of the boundary are settled by the FP64 test;
+//  5. the three folded beam maps are interpolated bilinearly at the
+//     orthographic grid coordinates (u, v) = (x, y) (Sec. 4.2) from 48-byte
+//     coefficient cells (read through L1/L2: grids of 100s of KB to MB);
+//  6. the Ludwig-3 angle (Appendix A) enters through
+//        e^{2 i chi} = e^{2 i zeta} (-e1 + i e2)^2 / sin^2(theta_k),
+//        e1 = Z_theta - x (Z_p + m), e2 = Z_phi - y (Z_p + m),
+//        m = (x Z_theta + y Z_phi) / (1 + k . p0),
+//     where (Z_theta, Z_phi, Z_p) is the sky pole in the antenna basis; e1 and
+//     e2 are z-components of the co- and cross-polar unit vectors
+//     (e_co . theta_k = -(e_co . z)/sin theta_k, e_co . phi_k = (k x e_co) . z / sin theta_k).
+//     e^{2 i zeta} is folded into the beam maps at plan time;
+//  7. per-sample FP32 partial sums: warp shuffles, then FP64 across warps.
+//
+// A pixel's sky value is loaded once per run and reused for all S samples.
+
+#include "pisco_internal.cuh"
+
+#include <climits>
+
+namespace pisco {
+
+constexpr int NT = 256;
+constexpr int NW = NT / 32;
+constexpr int RC = 128;  // rings per chunk of the union disc
+
+template <int S, int MODE>
+__global__ void __launch_bounds__(NT, 2) k_fast(const __grid_constant__ LaunchParams P) {
+    __shared__ double sTh[S], sPh[S], sPx[S], sPy[S], sPz[S];
+    __shared__ float4 sA[S];  // cos(b/2), sin(b/2), cos psi0, sin psi0   (b = phi0 - phi_c)
+    __shared__ float4 sB[S];  // cos theta0, sin theta0, Z_theta, Z_phi
+    __shared__ float sBf[S];  // b
+    __shared__ float sY[S];   // adjoint: tod * scale
+    __shared__ int sValid[S];
+    __shared__ int sGs[S], sGe[S];
+    __shared__ int sNg;
+    __shared__ double sPhiC;
+    __shared__ int sRlo, sRhi;
+    __shared__ float2 sPA[RC * S];  // per (ring, sample): sin(dtheta), 1 - cos(dtheta)
+    __shared__ float sLo[RC], sHi[RC];
+    __shared__ int sFlag[RC];
+    __shared__ int sJlo[RC], sJref[RC], sFirst[RC], sRc[RC], sPref[RC + 1], sWarpTot[RC / 32];
+    __shared__ float sAref[RC], sSr[RC], sInv[RC], sDph[RC];
+    __shared__ float sRed[NW][S];
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const float4* __restrict__ sky = (const float4*)P.sky;
+    const int nc = P.grid_n - 1;
+    const float gmax = (float)(P.grid_n - 2);
+
+    for (long long tile = blockIdx.x; tile < P.total_tiles; tile += gridDim.x) {
+        int d = 0;
+        while (d + 1 < P.ndet && P.det[d + 1].tile_begin <= tile) ++d;
+        const DetEntry& det = P.det[d];
+        const long long lt = tile - det.tile_begin;
+        const long long t0 = det.begin + lt * S;
+        const int ns = (int)min((long long)S, det.count - lt * S);
+        const float4* __restrict__ cells = (const float4*)det.beam;
+
+        // 1. per-sample constants
+        if (tid < S) {
+            const int i = tid;
+            bool ok = i < ns;
+            double th = 0.0, ph = 0.0, ps = 0.0;
+            if (ok) {
+                th = P.theta[t0 + i];
+                ph = P.phi[t0 + i];
+                ps = P.psi[t0 + i];
+                ok = isfinite(th) && isfinite(ph) && isfinite(ps) && th >= 0.0 && th <= kPi;
+            }
+            float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = make_float4(0.f, 0.f, 0.f, 0.f);
+            double px = 0.0, py = 0.0, pz = 0.0, phw = 0.0;
+            if (ok) {
+                phw = ph - kTwoPi * floor(ph / kTwoPi);
+                if (phw >= kTwoPi) phw -= kTwoPi;
+                double st, ct, sp, cp, ss, cs;
+                sincos(th, &st, &ct);
+                sincos(phw, &sp, &cp);
+                sincos(ps, &ss, &cs);
+                px = st * cp;
+                py = st * sp;
+                pz = ct;
+                a.z = (float)cs;
+                a.w = (float)ss;
+                b = make_float4((float)ct, (float)st, (float)(-cs * st), (float)(ss * st));
+                if (MODE == kAdjoint) sY[i] = (float)((double)((const float*)P.tod_in)[t0 + i] * det.scale);
+            }
+            sTh[i] = th;
+            sPh[i] = phw;
+            sPx[i] = px;
+            sPy[i] = py;
+            sPz[i] = pz;
+            sA[i] = a;
+            sB[i] = b;
+            sValid[i] = ok ? 1 : 0;
+        }
+        __syncthreads();
+
+        // 2. greedy grouping of nearby samples
+        if (tid == 0) {
+            int ng = 0, i = 0;
+            while (i < S) {
+                if (!sValid[i]) {
+                    ++i;
+                    continue;
+                }
+                int j = i + 1;
+                for (; j < S; ++j) {
+                    if (!sValid[j]) continue;
+                    const double c = sPx[i] * sPx[j] + sPy[i] * sPy[j] + sPz[i] * sPz[j];
+                    double db = sPh[j] - sPh[i];
+                    db -= kTwoPi * rint(db / kTwoPi);
+                    if (c < P.group_cos || fabs(db) > (double)P.group_dphi) break;
+                }
+                sGs[ng] = i;
+                sGe[ng] = j;
+                ++ng;
+                i = j;
+            }
+            sNg = ng;
+        }
+        __syncthreads();
+        const int ngroups = sNg;
+
+        for (int g = 0; g < ngroups; ++g) {
+            const int gs = sGs[g], ge = sGe[g];
+            if (tid < S && tid >= gs && tid < ge && sValid[tid]) {
+                double db = sPh[tid] - sPh[gs];
+                db -= kTwoPi * rint(db / kTwoPi);
+                double sb, cb;
+                sincos(0.5 * db, &sb, &cb);
+                sA[tid].x = (float)cb;
+                sA[tid].y = (float)sb;
+                sBf[tid] = (float)db;
+            }
+            if (tid == 0) {
+                sPhiC = sPh[gs];
+                double tmin = 1e9, tmax = -1e9;
+                for (int i = gs; i < ge; ++i)
+                    if (sValid[i]) {
+                        tmin = fmin(tmin, sTh[i]);
+                        tmax = fmax(tmax, sTh[i]);
+                    }
+                int ra, rb;
+                ring_range(tmin, tmax, P.radius, P.nside, &ra, &rb);
+                sRlo = ra;
+                sRhi = rb;
+            }
+            __syncthreads();
+
+            float acc[S];
+#pragma unroll
+            for (int i = 0; i < S; ++i) acc[i] = 0.f;
+
+            const int rlo = sRlo, rhi = sRhi;
+            for (int c0 = rlo; c0 <= rhi; c0 += RC) {
+                const int nr = min(RC, rhi - c0 + 1);
+
+                // 3. per (ring, sample) offsets and the union of the discs' longitude ranges
+                for (int item = tid; item < RC * S; item += NT) {
+                    const int ri = item / S, i = item % S;
+                    float lo = __int_as_float(0x7f800000), hi = -__int_as_float(0x7f800000);
+                    int full = 0;
+                    float2 pa = make_float2(0.f, 1e30f);
+                    if (ri < nr && i >= gs && i < ge && sValid[i]) {
+                        const RingInfo& R = P.rings[c0 + ri];
+                        const float h = (float)(0.5 * (R.theta - sTh[i]));
+                        float sh, ch;
+                        sincosf(h, &sh, &ch);
+                        const float av = 2.f * sh * sh;
+                        pa = make_float2(2.f * sh * ch, av);
+                        if (av <= P.wr_hi) {
+                            const float b2 = 2.f * sB[i].y * R.s_f;
+                            const float tau = (P.wr_hi - av) / b2;
+                            if (!(b2 > 0.f) || !(tau < 0.999f)) {
+                                full = 1;
+                            } else {
+                                const float hw = 2.f * asinf(sqrtf(fmaxf(tau, 0.f)));
+                                lo = sBf[i] - hw;
+                                hi = sBf[i] + hw;
+                            }
+                        }
+                    }
+                    sPA[item] = pa;
+#pragma unroll
+                    for (int off = S / 2; off > 0; off >>= 1) {
+                        lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, off, S));
+                        hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, off, S));
+                        full |= __shfl_xor_sync(0xffffffffu, full, off, S);
+                    }
+                    if (i == 0 && ri < nr) {
+                        sLo[ri] = lo;
+                        sHi[ri] = hi;
+                        sFlag[ri] = full ? 2 : (lo <= hi ? 1 : 0);
+                    }
+                }
+                __syncthreads();
+
+                // per ring: pixel index range of the union and its prefix sum
+                int cnt = 0;
+                if (tid < RC) {
+                    int jlo = 0, jref = 0, first = 0, rc = 1;
+                    float aref = 0.f, sr = 0.f, inv = 0.f, dph = 0.f;
+                    if (tid < nr) {
+                        const RingInfo& R = P.rings[c0 + tid];
+                        const int flag = sFlag[tid];
+                        first = (int)R.first;
+                        rc = R.count;
+                        sr = R.s_f;
+                        inv = R.inv_s2_f;
+                        dph = R.dphi_f;
+                        const double phic = sPhiC;
+                        jref = (int)rint((phic - R.phi0) / R.dphi);
+                        aref = (float)(R.phi0 + (double)jref * R.dphi - phic);
+                        if (flag == 2) {
+                            cnt = R.count;
+                            jlo = jref - R.count / 2;
+                        } else if (flag == 1) {
+                            const double ulo = (phic + (double)sLo[tid] - R.phi0) / R.dphi;
+                            const double uhi = (phic + (double)sHi[tid] - R.phi0) / R.dphi;
+                            const long long a = (long long)floor(ulo) - 1, b = (long long)ceil(uhi) + 1;
+                            if (b - a + 1 >= R.count) {
+                                cnt = R.count;
+                                jlo = jref - R.count / 2;
+                            } else {
+                                cnt = (int)(b - a + 1);
+                                jlo = (int)a;
+                            }
+                        }
+                    }
+                    sJlo[tid] = jlo;
+                    sJref[tid] = jref;
+                    sFirst[tid] = first;
+                    sRc[tid] = rc;
+                    sAref[tid] = aref;
+                    sSr[tid] = sr;
+                    sInv[tid] = inv;
+                    sDph[tid] = dph;
+                    int v = cnt;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int y = __shfl_up_sync(0xffffffffu, v, o);
+                        if (lane >= o) v += y;
+                    }
+                    if (lane == 31) sWarpTot[warp] = v;
+                    cnt = v;  // inclusive prefix within the warp
+                }
+                __syncthreads();
+                if (tid < RC) {
+                    int base = 0;
+                    for (int w = 0; w < warp; ++w) base += sWarpTot[w];
+                    sPref[tid + 1] = base + cnt;
+                    if (tid == 0) sPref[0] = 0;
+                }
+                __syncthreads();
+
+                // 4-7. pixels of the union x samples of the run
+                const int total = sPref[nr];
+                for (int f = tid; f < total; f += NT) {
+                    int lo_ = 0, hi_ = nr - 1;
+                    while (lo_ < hi_) {
+                        const int mid = (lo_ + hi_ + 1) >> 1;
+                        if (sPref[mid] <= f) lo_ = mid;
+                        else hi_ = mid - 1;
+                    }
+                    const int ri = lo_;
+                    const int j = sJlo[ri] + (f - sPref[ri]);
+                    const int rc = sRc[ri];
+                    int jw = j % rc;
+                    if (jw < 0) jw += rc;
+                    const long long pix = (long long)sFirst[ri] + jw;
+                    if (pix < 0 || pix >= P.npix) {  // cannot happen; recorded, never dereferenced
+                        atomicOr(P.err, 1);
+                        continue;
+                    }
+                    const float aa = fmaf((float)(j - sJref[ri]), sDph[ri], sAref[ri]);
+                    float sa, ca;
+                    sincosf(0.5f * aa, &sa, &ca);
+                    const float4 sk = __ldg(sky + pix);
+                    const float inv = sInv[ri];
+                    const float ip = sk.x, qp = sk.y * inv, up = sk.z * inv;
+                    const float sr2 = 2.f * sSr[ri];
+                    float gI = 0.f, gQ = 0.f, gU = 0.f;
+#pragma unroll
+                    for (int i = 0; i < S; ++i) {
+                        if (i < gs || i >= ge) continue;
+                        const float4 A4 = sA[i];
+                        const float4 B4 = sB[i];
+                        const float2 pa = sPA[ri * S + i];
+                        const float sh = fmaf(sa, A4.x, -ca * A4.y);  // sin(dphi / 2)
+                        const float ch = fmaf(ca, A4.x, sa * A4.y);   // cos(dphi / 2)
+                        const float sh2 = sh * sh;
+                        const float w = fmaf(B4.y * sr2, sh2, pa.y);  // 1 - k . p0
+                        if (w > P.wr_hi) continue;
+                        if (w > P.wr_lo &&
+                            !exact_in_disc(P.rings, c0 + ri, jw, sPx[i], sPy[i], sPz[i], P.cos_r))
+                            continue;
+                        if (MODE == kCount) {
+                            acc[i] += 1.f;
+                            continue;
+                        }
+                        const float x0 = fmaf(-B4.x * sr2, sh2, pa.x);
+                        const float y0 = sr2 * sh * ch;
+                        const float x = fmaf(A4.z, x0, A4.w * y0);   // k . theta'0
+                        const float y = fmaf(A4.z, y0, -A4.w * x0);  // k . phi'0
+                        const float fu = fmaf(x, P.invh_f, P.cg_f);
+                        const float fv = fmaf(y, P.invh_f, P.cg_f);
+                        const float flu = fminf(fmaxf(floorf(fu), 0.f), gmax);
+                        const float flv = fminf(fmaxf(floorf(fv), 0.f), gmax);
+                        const float fx = fmaf(x, P.invh_f, P.cg_f - flu);
+                        const float fy = fmaf(y, P.invh_f, P.cg_f - flv);
+                        const int cell = (int)flv * nc + (int)flu;
+                        const float4 ka = __ldg(cells + 3 * cell);
+                        const float4 kb = __ldg(cells + 3 * cell + 1);
+                        const float4 kc = __ldg(cells + 3 * cell + 2);
+                        const float bA = fmaf(fy, fmaf(fx, ka.w, ka.z), fmaf(fx, ka.y, ka.x));
+                        const float bB = fmaf(fy, fmaf(fx, kb.w, kb.z), fmaf(fx, kb.y, kb.x));
+                        const float bC = fmaf(fy, fmaf(fx, kc.w, kc.z), fmaf(fx, kc.y, kc.x));
+                        const float q = __frcp_rn(2.f - w);  // 1 / (1 + k . p0)
+                        const float mp = fmaf(q, fmaf(x, B4.z, y * B4.w), B4.x);
+                        const float e1 = fmaf(-x, mp, B4.z);
+                        const float e2 = fmaf(-y, mp, B4.w);
+                        const float re = fmaf(e1, e1, -e2 * e2);
+                        const float im2 = e1 * e2;
+                        if (MODE == kForward) {
+                            const float al = fmaf(re, qp, -2.f * im2 * up);
+                            const float be = fmaf(2.f * im2, qp, re * up);
+                            acc[i] = fmaf(bA, ip, fmaf(bB, al, fmaf(bC, be, acc[i])));
+                        } else {
+                            const float yv = sY[i];
+                            gI = fmaf(yv, bA, gI);
+                            gQ = fmaf(yv, fmaf(bB, re, 2.f * bC * im2), gQ);
+                            gU = fmaf(yv, fmaf(bC, re, -2.f * bB * im2), gU);
+                        }
+                    }
+                    if (MODE == kAdjoint) {
+                        if (gI != 0.f || gQ != 0.f || gU != 0.f) {
+                            float* maps = (float*)P.out;
+                            atomicAdd(maps + pix, gI);
+                            atomicAdd(maps + P.npix + pix, gQ * inv);
+                            atomicAdd(maps + 2 * P.npix + pix, gU * inv);
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+
+            if (MODE != kAdjoint) {
+#pragma unroll
+                for (int i = 0; i < S; ++i) {
+                    if (i < gs || i >= ge) continue;
+                    float v = acc[i];
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                    if (lane == 0) sRed[warp][i] = v;
+                }
+                __syncthreads();
+                if (tid >= gs && tid < ge && sValid[tid]) {
+                    double s = 0.0;
+#pragma unroll
+                    for (int w = 0; w < NW; ++w) s += (double)sRed[w][tid];
+                    if (MODE == kForward) ((float*)P.out)[t0 + tid] = (float)(det.scale * s);
+                    else P.counts[t0 + tid] = (int32_t)s;
+                }
+                __syncthreads();
+            }
+        }
+
+        if (tid < ns && !sValid[tid]) {
+            if (MODE == kForward) ((float*)P.out)[t0 + tid] = __int_as_float(0x7fc00000);
+            if (MODE == kCount) P.counts[t0 + tid] = -1;
+        }
+        __syncthreads();
+    }
+}
+
+template <int S>
+static cudaError_t launch_s(const LaunchParams& p, int mode, cudaStream_t s) {
+    if (p.total_tiles <= 0) return cudaSuccess;
+    const unsigned grid = (unsigned)min(p.total_tiles, (long long)INT_MAX);
+    switch (mode) {
+        case kForward: k_fast<S, kForward><<<grid, NT, 0, s>>>(p); break;
+        case kAdjoint: k_fast<S, kAdjoint><<<grid, NT, 0, s>>>(p); break;
+        default: k_fast<S, kCount><<<grid, NT, 0, s>>>(p); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fast(const LaunchParams& p, int mode, int tile_samples, cudaStream_t s) {
+    switch (tile_samples) {
+        case 8: return launch_s<8>(p, mode, s);
+        case 32: return launch_s<32>(p, mode, s);
+        default: return launch_s<16>(p, mode, s);
+    }
+}
+
+}  // namespace pisco

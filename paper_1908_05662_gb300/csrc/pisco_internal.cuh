@@ -1,0 +1,147 @@
+// Internal types shared by the translation units of libpisco.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pisco.h"
+
+namespace pisco {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kTwoPi = 6.28318530717958647692;
+
+// One HEALPix RING ring (Sec. 5.1).  FP64 geometry plus the FP32 copies the
+// fast path reads per pixel.
+struct RingInfo {
+    double z;         // cos(theta) of the ring
+    double s;         // sin(theta), from (1 - z)(1 + z) so it keeps precision near the poles
+    double theta;     // colatitude
+    double phi0;      // phi of pixel j = 0
+    double dphi;      // phi step
+    long long first;  // pixel number of j = 0
+    int count;        // pixels in the ring
+    float s_f;        // (float) s
+    float inv_s2_f;   // (float) 1 / s^2
+    float dphi_f;     // (float) dphi
+};
+static_assert(sizeof(RingInfo) == 64, "RingInfo layout");
+
+// One detector's slice of a launch.
+struct DetEntry {
+    long long begin;       // first sample, index into the pointing arrays
+    long long count;       // number of samples
+    long long tile_begin;  // first tile (block) index of this detector
+    const void* beam;      // FP32: float4 cells [(N-1)^2][3]; FP64: double nodes [3][N][N]
+    double scale;          // (s/2) Omega_pix / Omega~
+};
+
+constexpr int kMaxDetPerLaunch = 64;
+
+enum Mode { kForward = 0, kAdjoint = 1, kCount = 2 };
+
+// Parameters of the FP32 tile kernel and of the FP64 plain kernel (by value).
+struct LaunchParams {
+    const RingInfo* rings;
+    int nrings;
+    int nside;
+    long long npix;
+    const void* sky;       // FP32: float4 [npix] (I, Q, U, 0); FP64: double [3][npix]
+    int grid_n;
+    float invh_f, cg_f;    // FP32 path: 1 / h and (N - 1) / 2
+    double sin_r, h;       // FP64 path grid: sin(R) and node spacing
+    double radius, cos_r;
+    float wr_lo, wr_hi;    // (1 - cos R)(1 -/+ 2e-6): FP32 membership band
+    double group_cos;      // samples within this cosine share one disc traversal
+    float group_dphi;      // ... and within this longitude offset
+    const double* theta;
+    const double* phi;
+    const double* psi;
+    void* out;             // forward: tod; adjoint: maps [3][npix]
+    const void* tod_in;    // adjoint input
+    int32_t* counts;       // count mode output
+    int* err;
+    int ndet;
+    long long total_tiles;
+    DetEntry det[kMaxDetPerLaunch];
+};
+
+}  // namespace pisco
+
+struct pisco_plan {
+    int nside;
+    int nrings;
+    long long npix;
+    int n_det;
+    int grid_n;
+    int precision;
+    int tile_samples;
+    double radius;
+    double cos_r;
+    double omega_pix;
+    pisco::RingInfo* d_rings;
+    void* d_sky;       // float4 [npix] or double [3][npix]
+    void* d_beam;      // per detector FP32 cells or FP64 nodes, contiguous
+    size_t beam_stride;  // bytes per detector in d_beam
+    double* h_omega;
+    double* h_scale;
+    pisco_detector* h_dets;
+    int* d_err;
+    // staging for pisco_convolve_host
+    cudaStream_t hs[2];
+    cudaEvent_t he[2];
+    void* d_stage[2];
+    size_t stage_bytes;
+    char msg[512];
+};
+
+namespace pisco {
+
+// Launchers (defined in the kernel translation units).
+cudaError_t launch_fast(const LaunchParams& p, int mode, int tile_samples, cudaStream_t s);
+cudaError_t launch_plain(const LaunchParams& p, int mode, cudaStream_t s);
+cudaError_t launch_plan_kernels(pisco_plan* plan, const void* sky, int sky_dtype,
+                                const float* grids, cudaStream_t s, double* d_omega_out);
+
+void set_error(pisco_plan* plan, const char* fmt, ...);
+
+}  // namespace pisco
+
+namespace pisco {
+
+// Continuous RING ring number (1-based) of colatitude cosine z (inverse of the
+// ring heights of Sec. 5.1's scheme); used to bound the rings a disc can meet.
+static __device__ __forceinline__ double ring_number(double z, int nside) {
+    if (z > 2.0 / 3.0) return nside * sqrt(3.0 * (1.0 - z));
+    if (z < -2.0 / 3.0) return 4.0 * nside - nside * sqrt(3.0 * (1.0 + z));
+    return nside * (2.0 - 1.5 * z);
+}
+
+// 0-based ring index range [*ra, *rb] that contains every ring whose
+// colatitude lies within `radius` of [tmin, tmax].
+static __device__ __forceinline__ void ring_range(double tmin, double tmax, double radius, int nside,
+                                           int* ra, int* rb) {
+    const double za = cos(fmax(tmin - radius, 0.0));
+    const double zb = cos(fmin(tmax + radius, kPi));
+    int ia = (int)floor(ring_number(za, nside)) - 1;
+    int ib = (int)ceil(ring_number(zb, nside)) + 1;
+    if (ia < 1) ia = 1;
+    if (ib > 4 * nside - 1) ib = 4 * nside - 1;
+    *ra = ia - 1;
+    *rb = ib - 1;
+}
+
+// The disc membership test k . p0 >= cos(radius) in FP64, evaluated in one
+// fixed order without fused multiply-adds so every caller takes the same
+// decision for the same pixel and pointing.
+static __device__ __noinline__ bool exact_in_disc(const RingInfo* rings, int r, int jw, double px, double py,
+                                           double pz, double cos_r) {
+    const RingInfo& R = rings[r];
+    double sp, cp;
+    sincos(__dadd_rn(R.phi0, __dmul_rn((double)jw, R.dphi)), &sp, &cp);
+    const double d = __dadd_rn(__dadd_rn(__dmul_rn(__dmul_rn(R.s, cp), px), __dmul_rn(__dmul_rn(R.s, sp), py)),
+                               __dmul_rn(R.z, pz));
+    return d >= cos_r;
+}
+
+}  // namespace pisco

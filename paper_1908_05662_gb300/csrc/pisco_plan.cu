@@ -1,0 +1,187 @@
+// Plan-time kernels: HEALPix ring table, sky packing, beam folding, Omega~.
+//
+// Everything the hot path reads is built once here, on the device:
+//  * the RING ring table (Sec. 5.1; z, phi offset, pixel count per ring);
+//  * the sky as float4 (I, Q, U, 0) per pixel for the FP32 path, or three
+//    float64 rows for the plain path;
+//  * per detector, the six beamsor maps folded into the three that reach the
+//    TOD.  D(chi) Lambda(chi) = (s/2)[(1+eps), (1-eps), 0, 0] (eqs. M_pol,
+//    lambda_operator), so
+//        A  = (1+eps) B_TT + (1-eps) B_TQ
+//        Bq = (1+eps) B_QT + (1-eps) B_QQ
+//        Cu = (1+eps) B_UT + (1-eps) B_UQ,
+//    and the detector angle zeta enters chi = beta + zeta - sigma (Appendix A)
+//    only through exp(2 i zeta), folded in as Bq' + i Cu' = (Bq + i Cu) e^{2 i zeta}.
+//    Bilinear interpolation is linear, so folding before interpolating is exact.
+//    FP32 plans store each grid cell as its bilinear coefficients
+//    f(fx, fy) = c0 + c1 fx + c2 fy + c3 fx fy for the three maps (48 bytes);
+//    plain plans keep the folded node values in float64;
+//  * Omega~ = int B_TT dOmega (Sec. 3) by the trapezoid rule over the grid with
+//    the orthographic area element du dv / sqrt(1 - u^2 - v^2).
+
+#include "pisco_internal.cuh"
+
+namespace pisco {
+
+__global__ void k_rings(int nside, int nrings, RingInfo* out) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrings) return;
+    const long long n = nside;
+    const long long i = r + 1;
+    RingInfo R;
+    double omz;
+    if (i < n) {
+        omz = (double)(i * i) / (3.0 * (double)(n * n));
+        R.z = 1.0 - omz;
+        R.count = (int)(4 * i);
+        R.dphi = kPi / (2.0 * (double)i);
+        R.phi0 = 0.5 * R.dphi;
+        R.first = 2 * i * (i - 1);
+    } else if (i <= 3 * n) {
+        R.z = 4.0 / 3.0 - 2.0 * (double)i / (3.0 * (double)n);
+        omz = 1.0 - R.z;
+        R.count = (int)(4 * n);
+        R.dphi = kPi / (2.0 * (double)n);
+        R.phi0 = 0.5 * (double)((i - n + 1) % 2) * R.dphi;
+        R.first = 2 * n * (n - 1) + (i - n) * 4 * n;
+    } else {
+        const long long m = 4 * n - i;
+        double opz = (double)(m * m) / (3.0 * (double)(n * n));
+        R.z = -(1.0 - opz);
+        omz = 1.0 - R.z;
+        R.count = (int)(4 * m);
+        R.dphi = kPi / (2.0 * (double)m);
+        R.phi0 = 0.5 * R.dphi;
+        R.first = 12 * n * n - 2 * m * (m + 1);
+    }
+    R.s = sqrt(omz * (1.0 + R.z));
+    R.theta = atan2(R.s, R.z);
+    R.s_f = (float)R.s;
+    R.inv_s2_f = (float)(1.0 / (R.s * R.s));
+    R.dphi_f = (float)R.dphi;
+    out[r] = R;
+}
+
+template <typename T>
+__global__ void k_sky32(const T* __restrict__ sky, long long npix, float4* __restrict__ out) {
+    long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= npix) return;
+    out[p] = make_float4((float)sky[p], (float)sky[npix + p], (float)sky[2 * npix + p], 0.0f);
+}
+
+template <typename T>
+__global__ void k_sky64(const T* __restrict__ sky, long long npix, double* __restrict__ out) {
+    long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= 3 * npix) return;
+    out[p] = (double)sky[p];
+}
+
+struct Folded {
+    double a, b, c;
+};
+
+__device__ __forceinline__ Folded fold_node(const float* __restrict__ g, long long nn, long long idx,
+                                            double eps, double c2z, double s2z) {
+    // map order TT, QT, UT, TQ, QQ, UQ
+    double tt = g[idx], qt = g[nn + idx], ut = g[2 * nn + idx];
+    double tq = g[3 * nn + idx], qq = g[4 * nn + idx], uq = g[5 * nn + idx];
+    Folded f;
+    f.a = (1.0 + eps) * tt + (1.0 - eps) * tq;
+    double bq = (1.0 + eps) * qt + (1.0 - eps) * qq;
+    double cu = (1.0 + eps) * ut + (1.0 - eps) * uq;
+    f.b = bq * c2z - cu * s2z;
+    f.c = bq * s2z + cu * c2z;
+    return f;
+}
+
+__global__ void k_cells(const float* __restrict__ g, int n, double eps, double zeta,
+                        float4* __restrict__ cells) {
+    const int nc = n - 1;
+    long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (cell >= (long long)nc * nc) return;
+    const int i = (int)(cell % nc), j = (int)(cell / nc);
+    const long long nn = (long long)n * n;
+    double s2z, c2z;
+    sincos(2.0 * zeta, &s2z, &c2z);
+    Folded f00 = fold_node(g, nn, (long long)j * n + i, eps, c2z, s2z);
+    Folded f10 = fold_node(g, nn, (long long)j * n + i + 1, eps, c2z, s2z);
+    Folded f01 = fold_node(g, nn, (long long)(j + 1) * n + i, eps, c2z, s2z);
+    Folded f11 = fold_node(g, nn, (long long)(j + 1) * n + i + 1, eps, c2z, s2z);
+    cells[3 * cell + 0] = make_float4((float)f00.a, (float)(f10.a - f00.a), (float)(f01.a - f00.a),
+                                      (float)(f11.a - f10.a - f01.a + f00.a));
+    cells[3 * cell + 1] = make_float4((float)f00.b, (float)(f10.b - f00.b), (float)(f01.b - f00.b),
+                                      (float)(f11.b - f10.b - f01.b + f00.b));
+    cells[3 * cell + 2] = make_float4((float)f00.c, (float)(f10.c - f00.c), (float)(f01.c - f00.c),
+                                      (float)(f11.c - f10.c - f01.c + f00.c));
+}
+
+__global__ void k_nodes64(const float* __restrict__ g, int n, double eps, double zeta,
+                          double* __restrict__ nodes) {
+    const long long nn = (long long)n * n;
+    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= nn) return;
+    double s2z, c2z;
+    sincos(2.0 * zeta, &s2z, &c2z);
+    Folded f = fold_node(g, nn, idx, eps, c2z, s2z);
+    nodes[idx] = f.a;
+    nodes[nn + idx] = f.b;
+    nodes[2 * nn + idx] = f.c;
+}
+
+// One block; fixed per-thread order and a fixed tree, so the result is deterministic.
+__global__ void k_omega(const float* __restrict__ tt, int n, double sin_r, double* out) {
+    __shared__ double red[256];
+    const double h = 2.0 * sin_r / (double)(n - 1);
+    double acc = 0.0;
+    const long long nn = (long long)n * n;
+    for (long long idx = threadIdx.x; idx < nn; idx += blockDim.x) {
+        const int i = (int)(idx % n), j = (int)(idx / n);
+        const double u = sin_r * (2.0 * i / (double)(n - 1) - 1.0);
+        const double v = sin_r * (2.0 * j / (double)(n - 1) - 1.0);
+        const double w = ((i == 0 || i == n - 1) ? 0.5 : 1.0) * ((j == 0 || j == n - 1) ? 0.5 : 1.0);
+        acc += w * (double)tt[idx] / sqrt(1.0 - u * u - v * v);
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = red[0] * h * h;
+}
+
+static inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+cudaError_t launch_plan_kernels(pisco_plan* plan, const void* sky, int sky_dtype, const float* grids,
+                                cudaStream_t s, double* d_omega_out) {
+    k_rings<<<blocks_for(plan->nrings, 128), 128, 0, s>>>(plan->nside, plan->nrings, plan->d_rings);
+    const long long npix = plan->npix;
+    if (plan->precision == PISCO_FP32) {
+        if (sky_dtype == PISCO_DTYPE_F32)
+            k_sky32<float><<<blocks_for(npix, 256), 256, 0, s>>>((const float*)sky, npix, (float4*)plan->d_sky);
+        else
+            k_sky32<double><<<blocks_for(npix, 256), 256, 0, s>>>((const double*)sky, npix, (float4*)plan->d_sky);
+    } else {
+        if (sky_dtype == PISCO_DTYPE_F32)
+            k_sky64<float><<<blocks_for(3 * npix, 256), 256, 0, s>>>((const float*)sky, npix, (double*)plan->d_sky);
+        else
+            k_sky64<double><<<blocks_for(3 * npix, 256), 256, 0, s>>>((const double*)sky, npix, (double*)plan->d_sky);
+    }
+    const int n = plan->grid_n;
+    const long long nn = (long long)n * n;
+    for (int d = 0; d < plan->n_det; ++d) {
+        const float* g = grids + (long long)d * 6 * nn;
+        char* dst = (char*)plan->d_beam + (size_t)d * plan->beam_stride;
+        const pisco_detector& det = plan->h_dets[d];
+        if (plan->precision == PISCO_FP32) {
+            const long long nc = (long long)(n - 1) * (n - 1);
+            k_cells<<<blocks_for(nc, 256), 256, 0, s>>>(g, n, det.eps, det.zeta, (float4*)dst);
+        } else {
+            k_nodes64<<<blocks_for(nn, 256), 256, 0, s>>>(g, n, det.eps, det.zeta, (double*)dst);
+        }
+        k_omega<<<1, 256, 0, s>>>(g, n, sin(plan->radius), d_omega_out + d);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace pisco

@@ -1,0 +1,239 @@
+"""Thin Python binding of libpisco's C ABI (include/pisco.h).
+
+Functions carry the C names and only marshal arguments: torch tensors become
+device pointers, the current torch stream becomes the cudaStream_t, and a
+non-zero status raises ``PiscoError``.  Every step of the convolution runs in
+the CUDA library; there is no other implementation behind these calls, and
+they raise if the library was not built.
+"""
+
+import ctypes
+import os
+
+import torch
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libpisco.so")
+
+PISCO_OK, PISCO_EINVAL, PISCO_ENOMEM, PISCO_ECUDA, PISCO_ETIMEOUT, PISCO_EUNSUPPORTED, PISCO_EDEVICE = range(7)
+PISCO_FP64_PLAIN, PISCO_FP32 = 0, 1
+PISCO_DTYPE_F32, PISCO_DTYPE_F64 = 0, 1
+
+STATUS_NAMES = {0: "PISCO_OK", 1: "PISCO_EINVAL", 2: "PISCO_ENOMEM", 3: "PISCO_ECUDA",
+                4: "PISCO_ETIMEOUT", 5: "PISCO_EUNSUPPORTED", 6: "PISCO_EDEVICE"}
+
+# Entry points declared in include/pisco.h, checked by the CPU test suite.
+EXPORTS = ("pisco_plan_create", "pisco_plan_destroy", "pisco_last_error", "pisco_plan_omega",
+           "pisco_convolve", "pisco_convolve_batched", "pisco_adjoint", "pisco_disc_count",
+           "pisco_convolve_host", "pisco_sync_status")
+
+
+class PiscoError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class pisco_detector(ctypes.Structure):
+    _fields_ = [("zeta", ctypes.c_double), ("eps", ctypes.c_double), ("s_resp", ctypes.c_double)]
+
+
+class pisco_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("tile_samples", ctypes.c_int),
+                ("reserved0", ctypes.c_int), ("reserved1", ctypes.c_int)]
+
+
+_lib = None
+
+
+def load_library(path=LIB_PATH):
+    """Load libpisco.so once; raise if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with `python -m paper_1908_05662_gb300.build`")
+    lib = ctypes.CDLL(path)
+    vp, i64, c_int, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    sig = {
+        "pisco_plan_create": (c_int, [ctypes.POINTER(vp), c_int, dbl, vp, c_int, c_int,
+                                      ctypes.POINTER(pisco_detector), c_int, vp,
+                                      ctypes.POINTER(dbl), ctypes.POINTER(pisco_options), vp]),
+        "pisco_plan_destroy": (None, [vp]),
+        "pisco_last_error": (ctypes.c_char_p, [vp]),
+        "pisco_plan_omega": (c_int, [vp, c_int, ctypes.POINTER(dbl), ctypes.POINTER(dbl)]),
+        "pisco_convolve": (c_int, [vp, c_int, i64, vp, vp, vp, vp, vp]),
+        "pisco_convolve_batched": (c_int, [vp, c_int, ctypes.POINTER(i64), vp, vp, vp, vp, vp]),
+        "pisco_adjoint": (c_int, [vp, c_int, i64, vp, vp, vp, vp, vp, c_int, vp]),
+        "pisco_disc_count": (c_int, [vp, i64, vp, vp, vp, vp]),
+        "pisco_convolve_host": (c_int, [vp, c_int, i64, vp, vp, vp, vp]),
+        "pisco_sync_status": (c_int, [vp, vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _check(status, plan=None):
+    if status != PISCO_OK:
+        msg = load_library().pisco_last_error(plan)
+        raise PiscoError(status, msg.decode() if msg else "")
+
+
+def _f64(t):
+    if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise ValueError("pointing arrays must be contiguous float64 CUDA tensors")
+    return t
+
+
+def pisco_plan_create(nside, radius, sky, dets, beam_grids, omega_tilde=None,
+                      precision=PISCO_FP32, tile_samples=0):
+    """Create a plan; returns an opaque handle (int).  sky: (3, 12 nside^2) CUDA tensor
+    (float32 or float64); dets: list of (zeta, eps, s_resp); beam_grids: (n_det, 6, N, N)
+    float32 CUDA tensor."""
+    lib = load_library()
+    if sky.dtype not in (torch.float32, torch.float64) or not sky.is_cuda:
+        raise ValueError("sky must be a float32/float64 CUDA tensor")
+    if beam_grids.dtype != torch.float32 or not beam_grids.is_cuda:
+        raise ValueError("beam_grids must be a float32 CUDA tensor")
+    sky, beam_grids = sky.contiguous(), beam_grids.contiguous()  # the plan copies both
+    n_det = len(dets)
+    if beam_grids.dim() != 4 or beam_grids.shape[0] != n_det or beam_grids.shape[1] != 6 \
+            or beam_grids.shape[2] != beam_grids.shape[3]:
+        raise ValueError("beam_grids must have shape (n_det, 6, N, N)")
+    if tuple(sky.shape) != (3, 12 * nside * nside):
+        raise ValueError("sky must have shape (3, 12 nside^2)")
+    arr = (pisco_detector * n_det)(*[pisco_detector(*map(float, d)) for d in dets])
+    om = None if omega_tilde is None else (ctypes.c_double * n_det)(*map(float, omega_tilde))
+    opt = pisco_options(precision, tile_samples, 0, 0)
+    handle = ctypes.c_void_p()
+    st = lib.pisco_plan_create(ctypes.byref(handle), int(nside), float(radius), _ptr(sky),
+                               PISCO_DTYPE_F64 if sky.dtype == torch.float64 else PISCO_DTYPE_F32,
+                               n_det, arr, int(beam_grids.shape[-1]), _ptr(beam_grids), om,
+                               ctypes.byref(opt), _stream())
+    _check(st)
+    return handle.value
+
+
+def pisco_plan_destroy(plan):
+    load_library().pisco_plan_destroy(plan)
+
+
+def pisco_plan_omega(plan, det=0):
+    om, sc = ctypes.c_double(), ctypes.c_double()
+    _check(load_library().pisco_plan_omega(plan, det, ctypes.byref(om), ctypes.byref(sc)), plan)
+    return om.value, sc.value
+
+
+def pisco_convolve(plan, det, theta, phi, psi, tod):
+    n = theta.numel()
+    _check(load_library().pisco_convolve(plan, det, n, _ptr(_f64(theta)), _ptr(_f64(phi)),
+                                         _ptr(_f64(psi)), _ptr(tod), _stream()), plan)
+    return tod
+
+
+def pisco_convolve_batched(plan, offsets, theta, phi, psi, tod):
+    n_det = len(offsets) - 1
+    off = (ctypes.c_int64 * len(offsets))(*map(int, offsets))
+    _check(load_library().pisco_convolve_batched(plan, n_det, off, _ptr(_f64(theta)), _ptr(_f64(phi)),
+                                                 _ptr(_f64(psi)), _ptr(tod), _stream()), plan)
+    return tod
+
+
+def pisco_adjoint(plan, det, theta, phi, psi, tod, maps, accumulate=False):
+    n = theta.numel()
+    _check(load_library().pisco_adjoint(plan, det, n, _ptr(_f64(theta)), _ptr(_f64(phi)),
+                                        _ptr(_f64(psi)), _ptr(tod), _ptr(maps), int(bool(accumulate)),
+                                        _stream()), plan)
+    return maps
+
+
+def pisco_disc_count(plan, theta, phi, counts):
+    n = theta.numel()
+    _check(load_library().pisco_disc_count(plan, n, _ptr(_f64(theta)), _ptr(_f64(phi)), _ptr(counts),
+                                           _stream()), plan)
+    return counts
+
+
+def pisco_convolve_host(plan, det, h_theta, h_phi, h_psi, h_tod):
+    """Host-buffer variant: CPU tensors in, CPU tensor out (pinned memory overlaps copies)."""
+    for t in (h_theta, h_phi, h_psi, h_tod):
+        if t.is_cuda or not t.is_contiguous():
+            raise ValueError("pisco_convolve_host takes contiguous CPU tensors")
+    n = h_theta.numel()
+    _check(load_library().pisco_convolve_host(plan, det, n, _ptr(h_theta), _ptr(h_phi), _ptr(h_psi),
+                                              _ptr(h_tod)), plan)
+    return h_tod
+
+
+def pisco_sync_status(plan):
+    _check(load_library().pisco_sync_status(plan, _stream()), plan)
+
+
+class Plan:
+    """Owning wrapper: ``Plan(...)`` creates, ``close()`` / context exit destroys."""
+
+    def __init__(self, nside, radius, sky, dets, beam_grids, omega_tilde=None, precision=PISCO_FP32,
+                 tile_samples=0):
+        self.nside, self.radius, self.precision = nside, radius, precision
+        self.n_det = len(dets)
+        self.handle = pisco_plan_create(nside, radius, sky, dets, beam_grids, omega_tilde, precision,
+                                        tile_samples)
+
+    @property
+    def out_dtype(self):
+        return torch.float32 if self.precision == PISCO_FP32 else torch.float64
+
+    def omega(self, det=0):
+        return pisco_plan_omega(self.handle, det)
+
+    def convolve(self, theta, phi, psi, det=0, out=None):
+        out = torch.empty(theta.numel(), dtype=self.out_dtype, device=theta.device) if out is None else out
+        return pisco_convolve(self.handle, det, theta, phi, psi, out)
+
+    def convolve_batched(self, offsets, theta, phi, psi, out=None):
+        out = torch.empty(theta.numel(), dtype=self.out_dtype, device=theta.device) if out is None else out
+        return pisco_convolve_batched(self.handle, offsets, theta, phi, psi, out)
+
+    def adjoint(self, theta, phi, psi, tod, det=0, maps=None, accumulate=False):
+        if maps is None:
+            maps = torch.empty(3, 12 * self.nside ** 2, dtype=self.out_dtype, device=theta.device)
+        return pisco_adjoint(self.handle, det, theta, phi, psi, tod, maps, accumulate)
+
+    def disc_count(self, theta, phi):
+        counts = torch.empty(theta.numel(), dtype=torch.int32, device=theta.device)
+        return pisco_disc_count(self.handle, theta, phi, counts)
+
+    def convolve_host(self, theta, phi, psi, det=0, out=None):
+        out = torch.empty(theta.numel(), dtype=self.out_dtype) if out is None else out
+        return pisco_convolve_host(self.handle, det, theta, phi, psi, out)
+
+    def sync_status(self):
+        pisco_sync_status(self.handle)
+
+    def close(self):
+        if self.handle:
+            pisco_plan_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -256,7 +256,7 @@ def gaussian_beam_maps(n, radius, fwhm_deg, ellipticity=0.0, xpol=0.0, sidelobe=
     else:
         maps[0] = (1.0 + xpol) * g
         maps[4] = (1.0 - xpol) * g
-    return maps.astype(np.float32)
+    return np.ascontiguousarray(maps, dtype=np.float32)
 
 
 def random_beam_maps(n, seed, smooth=True):
@@ -277,4 +277,4 @@ def random_beam_maps(n, seed, smooth=True):
             maps = (np.apply_along_axis(lambda a: np.convolve(a, k, "same"), -2, maps))
     maps[0] = bump * (1.0 + 0.3 * np.tanh(maps[0]))
     maps[1:] = 0.2 * bump * maps[1:]
-    return maps.astype(np.float32)
+    return np.ascontiguousarray(maps, dtype=np.float32)

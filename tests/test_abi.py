@@ -1,0 +1,60 @@
+"""The C-ABI library builds, loads and exports every entry point of include/pisco.h (CPU only)."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1908_05662_gb300 import pisco
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(pisco.LIB_PATH):
+        from paper_1908_05662_gb300.build import build_library
+        build_library()
+    return pisco.load_library()
+
+
+def _declared():
+    with open(os.path.join(ROOT, "include", "pisco.h")) as f:
+        text = f.read()
+    return set(re.findall(r"^(?:pisco_status|void|const char\*)\s+(pisco_\w+)\s*\(", text, re.M))
+
+
+def test_header_declares_the_binding_exports():
+    assert _declared() == set(pisco.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_create_rejects_bad_arguments_before_touching_the_device(lib):
+    handle = ctypes.c_void_p()
+    det = (pisco.pisco_detector * 1)(pisco.pisco_detector(0.0, 0.0, 1.0))
+    cases = [
+        dict(nside=0, radius=0.1), dict(nside=9000, radius=0.1),
+        dict(nside=8, radius=0.0), dict(nside=8, radius=2.0),
+        dict(nside=8, radius=0.1, n_det=0), dict(nside=8, radius=0.1, grid_n=1),
+        dict(nside=8, radius=0.1, dtype=7),
+    ]
+    for c in cases:
+        st = lib.pisco_plan_create(ctypes.byref(handle), c["nside"], c["radius"], ctypes.c_void_p(16),
+                                   c.get("dtype", 0), c.get("n_det", 1), det, c.get("grid_n", 11),
+                                   ctypes.c_void_p(16), None, None, None)
+        assert st == pisco.PISCO_EINVAL, c
+        assert handle.value is None
+        assert lib.pisco_last_error(None)
+
+
+def test_calls_on_a_null_plan_are_rejected(lib):
+    assert lib.pisco_convolve(None, 0, 0, None, None, None, None, None) == pisco.PISCO_EINVAL
+    assert lib.pisco_adjoint(None, 0, 0, None, None, None, None, None, 0, None) == pisco.PISCO_EINVAL
+    assert lib.pisco_disc_count(None, 0, None, None, None, None) == pisco.PISCO_EINVAL
+    assert lib.pisco_sync_status(None, None) == pisco.PISCO_EINVAL
+    lib.pisco_plan_destroy(None)
