@@ -43,7 +43,8 @@ UNIT = "samples/s"
 WORKLOAD = dict(workload="single-detector FP32: nside 512 sky, 1.5 deg beam + 1% sidelobe ring at 6-8 deg "
                          "+ 0.5% cross-polar, 6 maps on 501x501 grid of radius 10 deg, 1e7 samples of a "
                          "45 deg elevation azimuth scan",
-                nside=512, radius_deg=10.0, grid_n=501, n_samples=10_000_000, tile_samples=16)
+                nside=512, radius_deg=10.0, grid_n=501, n_samples=10_000_000, tile_samples=16,
+                pixels_per_thread=1)
 
 # FP32 operations per in-disc (sample, pixel) pair in the forward kernel's inner loop
 # (FMA = 2): half-angle rotation 7, disc test 3, in-frame offsets 11, grid index 10,
@@ -123,9 +124,24 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
+def cached_sky(nside, seed, device):
+    """The synthetic sky, kept in a temp-dir file so repeated runs on one machine
+    (a plain run, then the same command under a profiler) skip the synthesis."""
+    import tempfile
+    path = os.path.join(tempfile.gettempdir(), "pisco_bench_cache",
+                        f"sky_n{nside}_s{seed}_{torch.device(device).type}.pt")
+    if os.path.exists(path):
+        return torch.load(path, map_location=device)
+    sky = sy.gaussian_sky(nside, seed, device=device)
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    torch.save(sky, path + ".tmp")
+    os.replace(path + ".tmp", path)
+    return sky
+
+
 def make_workload(device, n):
     r = math.radians(WORKLOAD["radius_deg"])
-    sky = sy.gaussian_sky(WORKLOAD["nside"], 1, device=device)
+    sky = cached_sky(WORKLOAD["nside"], 1, device)
     grids = sy.gaussian_beam_maps(WORKLOAD["grid_n"], r, 1.5, ellipticity=0.0, xpol=0.005,
                                   sidelobe=(0.01, 7.0, 0.5))
     theta, phi, psi = sy.ces_scan(n, device=device)
@@ -156,7 +172,10 @@ def run_reference(args, rank, world):
         return
     torch.set_num_threads(1)
     n = 2000
-    r, sky, grids, (th, ph, ps) = make_workload("cpu", n)
+    # inputs are made on the GPU when there is one (the synthesis is slow on the host)
+    gen_dev = "cuda" if torch.cuda.is_available() else "cpu"
+    r, sky, grids, (th, ph, ps) = make_workload(gen_dev, n)
+    sky, th, ph, ps = sky.cpu(), th.cpu(), ph.cpu(), ps.cpu()
     thn, phn, psn = th.numpy(), ph.numpy(), ps.numpy()
     det = (0.0, 0.0, 1.0)
     per_step = 4
@@ -199,7 +218,7 @@ def main():
     det = (0.0, 0.0, 1.0)
     g = torch.as_tensor(grids, device=dev)[None].contiguous()
     plan = pisco.Plan(WORKLOAD["nside"], r, sky, [det], g, precision=pisco.PISCO_FP32,
-                      tile_samples=WORKLOAD["tile_samples"])
+                      tile_samples=WORKLOAD["tile_samples"], pixels_per_thread=WORKLOAD["pixels_per_thread"])
     tod = torch.empty(n, dtype=torch.float32, device=dev)
 
     # exact number of in-disc pairs (untimed): the kernel's own disc counts

@@ -59,7 +59,9 @@ typedef enum pisco_status {
     PISCO_EDEVICE = 6        /* a kernel recorded an invariant violation */
 } pisco_status;
 
-/* Arithmetic of a plan (pisco_options.precision). */
+/* Arithmetic of a plan (pisco_options.precision).  tile_samples and
+ * pixels_per_thread change only the work split of the FP32 kernel (results
+ * differ at FP32 rounding level), never the arithmetic. */
 enum {
     PISCO_FP64_PLAIN = 0, /* FP64 throughout, one CTA per sample: the plain reference path */
     PISCO_FP32 = 1        /* FP32 arithmetic, FP64 only where offsets would cancel */
@@ -79,10 +81,15 @@ typedef struct pisco_detector {
 
 typedef struct pisco_options {
     int precision;     /* PISCO_FP64_PLAIN or PISCO_FP32 */
-    int tile_samples;  /* FP32 path: consecutive samples sharing one disc traversal: 8, 16 or 32 (0 = 16) */
-    int reserved0;
-    int reserved1;
+    int tile_samples;       /* FP32 path: consecutive samples sharing one disc traversal: 8, 16 or 32 (0 = 16) */
+    int pixels_per_thread;  /* FP32 path: consecutive ring pixels per thread: 1 or 2 (0 = 1) */
+    int beam_fetch;         /* FP32 path: PISCO_FETCH_CELLS or PISCO_FETCH_TEXTURE (0 = cells) */
 } pisco_options;
+
+/* How the FP32 kernel reads the beam (pisco_options.beam_fetch): 64-byte
+ * bilinear-coefficient cells through L1/L2, or 2 x 2 texel gathers of the
+ * folded node maps through the texture path.  Same arithmetic either way. */
+enum { PISCO_FETCH_TEXTURE = 1, PISCO_FETCH_CELLS = 2 };
 
 typedef struct pisco_plan pisco_plan;  /* opaque, owned by the library */
 

@@ -50,6 +50,14 @@ static void free_plan(pisco_plan* p) {
     cudaFree(p->d_sky);
     cudaFree(p->d_beam);
     cudaFree(p->d_err);
+    if (p->h_tex)
+        for (int k = 0; k < 3 * p->n_det; ++k)
+            if (p->h_tex[k]) cudaDestroyTextureObject(p->h_tex[k]);
+    if (p->h_arrays)
+        for (int k = 0; k < 3 * p->n_det; ++k)
+            if (p->h_arrays[k]) cudaFreeArray(p->h_arrays[k]);
+    free(p->h_tex);
+    free(p->h_arrays);
     for (int k = 0; k < 2; ++k) {
         if (p->hs[k]) cudaStreamDestroy(p->hs[k]);
         if (p->he[k]) cudaEventDestroy(p->he[k]);
@@ -110,6 +118,16 @@ extern "C" pisco_status pisco_plan_create(pisco_plan** out, int nside, double ra
         set_error(nullptr, "tile_samples %d is not 8, 16 or 32", tile);
         return PISCO_EINVAL;
     }
+    int np = opt && opt->pixels_per_thread ? opt->pixels_per_thread : 1;
+    if (np != 1 && np != 2) {
+        set_error(nullptr, "pixels_per_thread %d is not 1 or 2", np);
+        return PISCO_EINVAL;
+    }
+    int fetch = opt && opt->beam_fetch ? opt->beam_fetch : PISCO_FETCH_CELLS;
+    if (fetch != PISCO_FETCH_TEXTURE && fetch != PISCO_FETCH_CELLS) {
+        set_error(nullptr, "beam_fetch %d is not PISCO_FETCH_TEXTURE or PISCO_FETCH_CELLS", fetch);
+        return PISCO_EINVAL;
+    }
     if (!is_device_ptr(sky) || !is_device_ptr(beam_grids)) {
         set_error(nullptr, "sky and beam_grids must be device pointers");
         return PISCO_EINVAL;
@@ -127,6 +145,8 @@ extern "C" pisco_status pisco_plan_create(pisco_plan** out, int nside, double ra
     p->grid_n = grid_n;
     p->precision = precision;
     p->tile_samples = tile;
+    p->pixels_per_thread = np;
+    p->beam_fetch = fetch;
     p->radius = radius_rad;
     p->cos_r = cos(radius_rad);
     p->omega_pix = 4.0 * kPi / (double)p->npix;
@@ -142,12 +162,14 @@ extern "C" pisco_status pisco_plan_create(pisco_plan** out, int nside, double ra
 
     const size_t nn = (size_t)grid_n * grid_n;
     const size_t nc = (size_t)(grid_n - 1) * (grid_n - 1);
-    p->beam_stride = precision == PISCO_FP32 ? nc * 3 * sizeof(float4) : 3 * nn * sizeof(double);
+    if (precision == PISCO_FP64_PLAIN) p->beam_stride = 3 * nn * sizeof(double);
+    else if (fetch == PISCO_FETCH_CELLS) p->beam_stride = nc * 4 * sizeof(float4);
+    else p->beam_stride = 0;
     const size_t sky_bytes = precision == PISCO_FP32 ? p->npix * sizeof(float4) : 3 * p->npix * sizeof(double);
     double* d_omega = nullptr;
     cudaError_t e = cudaMalloc(&p->d_rings, p->nrings * sizeof(RingInfo));
     if (e == cudaSuccess) e = cudaMalloc(&p->d_sky, sky_bytes);
-    if (e == cudaSuccess) e = cudaMalloc(&p->d_beam, p->beam_stride * n_det);
+    if (e == cudaSuccess && p->beam_stride) e = cudaMalloc(&p->d_beam, p->beam_stride * n_det);
     if (e == cudaSuccess) e = cudaMalloc(&p->d_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&d_omega, n_det * sizeof(double));
     if (e != cudaSuccess) {
@@ -160,6 +182,42 @@ extern "C" pisco_status pisco_plan_create(pisco_plan** out, int nside, double ra
     cudaStream_t s = (cudaStream_t)stream;
     e = cudaMemsetAsync(p->d_err, 0, sizeof(int), s);
     if (e == cudaSuccess) e = launch_plan_kernels(p, sky, sky_dtype, beam_grids, s, d_omega);
+    if (e == cudaSuccess && precision == PISCO_FP32 && fetch == PISCO_FETCH_TEXTURE) {
+        // folded node maps A, Bq', Cu' of every detector as 2-D float textures
+        p->h_arrays = (cudaArray_t*)calloc(3 * (size_t)n_det, sizeof(cudaArray_t));
+        p->h_tex = (cudaTextureObject_t*)calloc(3 * (size_t)n_det, sizeof(cudaTextureObject_t));
+        float* d_tmp = nullptr;
+        if (!p->h_arrays || !p->h_tex) e = cudaErrorMemoryAllocation;
+        if (e == cudaSuccess) e = cudaMalloc(&d_tmp, 3 * nn * sizeof(float));
+        const cudaChannelFormatDesc desc = cudaCreateChannelDesc<float>();
+        for (int d = 0; d < n_det && e == cudaSuccess; ++d) {
+            e = launch_fold_nodes32(beam_grids + (size_t)d * 6 * nn, grid_n, dets[d].eps, dets[d].zeta, d_tmp, s);
+            for (int m = 0; m < 3 && e == cudaSuccess; ++m) {
+                cudaArray_t arr = nullptr;
+                e = cudaMallocArray(&arr, &desc, grid_n, grid_n);
+                if (e != cudaSuccess) break;
+                p->h_arrays[3 * d + m] = arr;
+                e = cudaMemcpy2DToArrayAsync(arr, 0, 0, d_tmp + m * nn, grid_n * sizeof(float),
+                                             grid_n * sizeof(float), grid_n, cudaMemcpyDeviceToDevice, s);
+                if (e != cudaSuccess) break;
+                cudaResourceDesc rd;
+                memset(&rd, 0, sizeof(rd));
+                rd.resType = cudaResourceTypeArray;
+                rd.res.array.array = arr;
+                cudaTextureDesc td;
+                memset(&td, 0, sizeof(td));
+                td.addressMode[0] = cudaAddressModeClamp;
+                td.addressMode[1] = cudaAddressModeClamp;
+                td.filterMode = cudaFilterModePoint;
+                td.readMode = cudaReadModeElementType;
+                td.normalizedCoords = 0;
+                e = cudaCreateTextureObject(&p->h_tex[3 * d + m], &rd, &td, nullptr);
+            }
+            // the next detector reuses d_tmp: finish this one's copies first
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        }
+        cudaFree(d_tmp);
+    }
     if (e == cudaSuccess) e = cudaMemcpyAsync(p->h_omega, d_omega, n_det * sizeof(double), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaFree(d_omega);
@@ -259,15 +317,19 @@ static pisco_status run(pisco_plan* plan, int mode, int d0, int nd, const int64_
             e.begin = begin[c + j];
             e.count = count[c + j];
             e.tile_begin = tiles;
-            e.beam = (const char*)plan->d_beam + (size_t)d * plan->beam_stride;
+            e.beam = plan->d_beam ? (const char*)plan->d_beam + (size_t)d * plan->beam_stride : nullptr;
             e.scale = plan->h_scale[d];
+            for (int m = 0; m < 3; ++m) e.tex[m] = plan->h_tex ? plan->h_tex[3 * d + m] : 0;
             tiles += (e.count + per_tile - 1) / per_tile;
         }
         if (k == 0) continue;
         L.ndet = k;
         L.total_tiles = tiles;
-        cudaError_t e = plan->precision == PISCO_FP32 ? launch_fast(L, mode, plan->tile_samples, s)
-                                                      : launch_plain(L, mode, s);
+        cudaError_t e;
+        if (plan->precision == PISCO_FP64_PLAIN) e = launch_plain(L, mode, s);
+        else if (plan->beam_fetch == PISCO_FETCH_CELLS)
+            e = launch_fast_cells(L, mode, plan->tile_samples, plan->pixels_per_thread, s);
+        else e = launch_fast_texture(L, mode, plan->tile_samples, plan->pixels_per_thread, s);
         if (e != cudaSuccess) {
             set_error(plan, "kernel launch failed: %s", cudaGetErrorString(e));
             return PISCO_ECUDA;

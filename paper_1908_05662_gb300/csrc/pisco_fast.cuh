@@ -21,8 +21,10 @@
 //  4. disc membership 1 - k . p0 <= 1 - cos R is decided in FP32; pairs
 //     within 2e-6 (relative) of the boundary are settled by the FP64 test;
 //  5. the three folded beam maps are interpolated bilinearly at the
-//     orthographic grid coordinates (u, v) = (x, y) (Sec. 4.2) from 48-byte
-//     coefficient cells (read through L1/L2: grids of 100s of KB to MB);
+//     orthographic grid coordinates (u, v) = (x, y) (Sec. 4.2), either from
+//     64-byte coefficient cells read through L1/L2 (one 32-byte and one
+//     16-byte load) or from 2 x 2 texel gathers of the node maps through the
+//     texture path (grids of 100s of KB to MB, read at scattered cells);
 //  6. the Ludwig-3 angle (Appendix A) enters through
 //        e^{2 i chi} = e^{2 i zeta} (-e1 + i e2)^2 / sin^2(theta_k),
 //        e1 = Z_theta - x (Z_p + m), e2 = Z_phi - y (Z_p + m),
@@ -33,7 +35,11 @@
 //     e^{2 i zeta} is folded into the beam maps at plan time;
 //  7. per-sample FP32 partial sums: warp shuffles, then FP64 across warps.
 //
-// A pixel's sky value is loaded once per run and reused for all S samples.
+// A thread takes NP consecutive pixels of a ring: their sky values are loaded
+// once per group and reused for all S samples, and each per-sample value read
+// from shared memory serves NP pairs.
+
+#pragma once
 
 #include "pisco_internal.cuh"
 
@@ -45,7 +51,40 @@ constexpr int NT = 256;
 constexpr int NW = NT / 32;
 constexpr int RC = 128;  // rings per chunk of the union disc
 
-template <int S, int MODE>
+// 1 / x from the hardware reciprocal (about 1 ulp); it only scales the small
+// correction m of the Ludwig-3 components, where 1e-7 relative is plenty.
+static __device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Bilinear value from a 2 x 2 texel gather, whose components are the nodes
+// (i, j+1), (i+1, j+1), (i+1, j), (i, j) in that order.
+static __device__ __forceinline__ float lerp_gather(const float4 g, float fx, float fy) {
+    const float lo = fmaf(fx, g.z - g.w, g.w);  // row j
+    const float hi = fmaf(fx, g.y - g.x, g.x);  // row j + 1
+    return fmaf(fy, hi - lo, lo);
+}
+
+// Beam-cell loads: one 32-byte (256-bit vector, sm_100 and later) and one
+// 16-byte read-only load per 64-byte cell, one sector each.  Cells are read at
+// scattered places (the L1 hit rate is low), so they are not allocated in L1.
+static __device__ __forceinline__ void ld_nc_v8(const float* p, float4& a, float4& b) {
+    asm("ld.global.nc.L1::no_allocate.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+        : "l"(p));
+}
+
+static __device__ __forceinline__ float4 ld_nc_v4(const float* p) {
+    float4 a;
+    asm("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
+        : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w)
+        : "l"(p));
+    return a;
+}
+
+template <int S, int NP, int FETCH, int MODE>
 __global__ void __launch_bounds__(NT, 2) k_fast(const __grid_constant__ LaunchParams P) {
     __shared__ double sTh[S], sPh[S], sPx[S], sPy[S], sPz[S];
     __shared__ float4 sA[S];  // cos(b/2), sin(b/2), cos psi0, sin psi0   (b = phi0 - phi_c)
@@ -60,7 +99,7 @@ __global__ void __launch_bounds__(NT, 2) k_fast(const __grid_constant__ LaunchPa
     __shared__ float2 sPA[RC * S];  // per (ring, sample): sin(dtheta), 1 - cos(dtheta)
     __shared__ float sLo[RC], sHi[RC];
     __shared__ int sFlag[RC];
-    __shared__ int sJlo[RC], sJref[RC], sFirst[RC], sRc[RC], sPref[RC + 1], sWarpTot[RC / 32];
+    __shared__ int sJlo[RC], sJref[RC], sFirst[RC], sRc[RC], sCnt[RC], sPref[RC + 1], sWarpTot[RC / 32];
     __shared__ float sAref[RC], sSr[RC], sInv[RC], sDph[RC];
     __shared__ float sRed[NW][S];
 
@@ -76,7 +115,7 @@ __global__ void __launch_bounds__(NT, 2) k_fast(const __grid_constant__ LaunchPa
         const long long lt = tile - det.tile_begin;
         const long long t0 = det.begin + lt * S;
         const int ns = (int)min((long long)S, det.count - lt * S);
-        const float4* __restrict__ cells = (const float4*)det.beam;
+        const float* __restrict__ cells = (const float*)det.beam;
 
         // 1. per-sample constants
         if (tid < S) {
@@ -217,7 +256,8 @@ __global__ void __launch_bounds__(NT, 2) k_fast(const __grid_constant__ LaunchPa
                 }
                 __syncthreads();
 
-                // per ring: pixel index range of the union and its prefix sum
+                // per ring: pixel index range of the union; the prefix sum counts runs
+                // of NP consecutive ring pixels (the last run of a ring is masked)
                 int cnt = 0;
                 if (tid < RC) {
                     int jlo = 0, jref = 0, first = 0, rc = 1;
@@ -253,18 +293,19 @@ __global__ void __launch_bounds__(NT, 2) k_fast(const __grid_constant__ LaunchPa
                     sJref[tid] = jref;
                     sFirst[tid] = first;
                     sRc[tid] = rc;
+                    sCnt[tid] = cnt;
                     sAref[tid] = aref;
                     sSr[tid] = sr;
                     sInv[tid] = inv;
                     sDph[tid] = dph;
-                    int v = cnt;
+                    int v = (cnt + NP - 1) / NP;
 #pragma unroll
                     for (int o = 1; o < 32; o <<= 1) {
                         const int y = __shfl_up_sync(0xffffffffu, v, o);
                         if (lane >= o) v += y;
                     }
                     if (lane == 31) sWarpTot[warp] = v;
-                    cnt = v;  // inclusive prefix within the warp
+                    cnt = v;  // inclusive prefix of runs within the warp
                 }
                 __syncthreads();
                 if (tid < RC) {
@@ -275,91 +316,129 @@ __global__ void __launch_bounds__(NT, 2) k_fast(const __grid_constant__ LaunchPa
                 }
                 __syncthreads();
 
-                // 4-7. pixels of the union x samples of the run
-                const int total = sPref[nr];
-                for (int f = tid; f < total; f += NT) {
+                // 4-7. runs of NP pixels x samples of the group: every per-sample value
+                // read from shared memory serves NP pairs from registers
+                const int totalq = sPref[nr];
+                for (int qd = tid; qd < totalq; qd += NT) {
                     int lo_ = 0, hi_ = nr - 1;
                     while (lo_ < hi_) {
                         const int mid = (lo_ + hi_ + 1) >> 1;
-                        if (sPref[mid] <= f) lo_ = mid;
+                        if (sPref[mid] <= qd) lo_ = mid;
                         else hi_ = mid - 1;
                     }
                     const int ri = lo_;
-                    const int j = sJlo[ri] + (f - sPref[ri]);
-                    const int rc = sRc[ri];
-                    int jw = j % rc;
-                    if (jw < 0) jw += rc;
-                    const long long pix = (long long)sFirst[ri] + jw;
-                    if (pix < 0 || pix >= P.npix) {  // cannot happen; recorded, never dereferenced
-                        atomicOr(P.err, 1);
-                        continue;
-                    }
-                    const float aa = fmaf((float)(j - sJref[ri]), sDph[ri], sAref[ri]);
-                    float sa, ca;
-                    sincosf(0.5f * aa, &sa, &ca);
-                    const float4 sk = __ldg(sky + pix);
-                    const float inv = sInv[ri];
-                    const float ip = sk.x, qp = sk.y * inv, up = sk.z * inv;
+                    const int off0 = (qd - sPref[ri]) * NP;
+                    const int cnt_r = sCnt[ri], rc = sRc[ri], jlo = sJlo[ri], jref = sJref[ri], first = sFirst[ri];
+                    const float aref = sAref[ri], dph = sDph[ri], inv = sInv[ri];
                     const float sr2 = 2.f * sSr[ri];
-                    float gI = 0.f, gQ = 0.f, gU = 0.f;
+                    float sa[NP], ca[NP], ip[NP], qp[NP], up[NP];
+                    int jw[NP];
+                    bool ok[NP];
+#pragma unroll
+                    for (int p4 = 0; p4 < NP; ++p4) {
+                        const int j = jlo + off0 + p4;
+                        int w = j % rc;
+                        if (w < 0) w += rc;
+                        jw[p4] = w;
+                        ok[p4] = off0 + p4 < cnt_r;
+                        const float aa = fmaf((float)(j - jref), dph, aref);
+                        sincosf(0.5f * aa, &sa[p4], &ca[p4]);
+                        float4 sk = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (ok[p4]) sk = __ldg(sky + first + w);
+                        ip[p4] = sk.x;
+                        qp[p4] = sk.y * inv;
+                        up[p4] = sk.z * inv;
+                    }
+                    int lastcell[NP];
+                    float4 cka[NP], ckb[NP], ckc[NP];
+#pragma unroll
+                    for (int p4 = 0; p4 < NP; ++p4) lastcell[p4] = -1;
+                    float gI[NP], gQ[NP], gU[NP];
+#pragma unroll
+                    for (int p4 = 0; p4 < NP; ++p4) gI[p4] = gQ[p4] = gU[p4] = 0.f;
 #pragma unroll
                     for (int i = 0; i < S; ++i) {
                         if (i < gs || i >= ge) continue;
                         const float4 A4 = sA[i];
                         const float4 B4 = sB[i];
                         const float2 pa = sPA[ri * S + i];
-                        const float sh = fmaf(sa, A4.x, -ca * A4.y);  // sin(dphi / 2)
-                        const float ch = fmaf(ca, A4.x, sa * A4.y);   // cos(dphi / 2)
-                        const float sh2 = sh * sh;
-                        const float w = fmaf(B4.y * sr2, sh2, pa.y);  // 1 - k . p0
-                        if (w > P.wr_hi) continue;
-                        if (w > P.wr_lo &&
-                            !exact_in_disc(P.rings, c0 + ri, jw, sPx[i], sPy[i], sPz[i], P.cos_r))
-                            continue;
-                        if (MODE == kCount) {
-                            acc[i] += 1.f;
-                            continue;
-                        }
-                        const float x0 = fmaf(-B4.x * sr2, sh2, pa.x);
-                        const float y0 = sr2 * sh * ch;
-                        const float x = fmaf(A4.z, x0, A4.w * y0);   // k . theta'0
-                        const float y = fmaf(A4.z, y0, -A4.w * x0);  // k . phi'0
-                        const float fu = fmaf(x, P.invh_f, P.cg_f);
-                        const float fv = fmaf(y, P.invh_f, P.cg_f);
-                        const float flu = fminf(fmaxf(floorf(fu), 0.f), gmax);
-                        const float flv = fminf(fmaxf(floorf(fv), 0.f), gmax);
-                        const float fx = fmaf(x, P.invh_f, P.cg_f - flu);
-                        const float fy = fmaf(y, P.invh_f, P.cg_f - flv);
-                        const int cell = (int)flv * nc + (int)flu;
-                        const float4 ka = __ldg(cells + 3 * cell);
-                        const float4 kb = __ldg(cells + 3 * cell + 1);
-                        const float4 kc = __ldg(cells + 3 * cell + 2);
-                        const float bA = fmaf(fy, fmaf(fx, ka.w, ka.z), fmaf(fx, ka.y, ka.x));
-                        const float bB = fmaf(fy, fmaf(fx, kb.w, kb.z), fmaf(fx, kb.y, kb.x));
-                        const float bC = fmaf(fy, fmaf(fx, kc.w, kc.z), fmaf(fx, kc.y, kc.x));
-                        const float q = __frcp_rn(2.f - w);  // 1 / (1 + k . p0)
-                        const float mp = fmaf(q, fmaf(x, B4.z, y * B4.w), B4.x);
-                        const float e1 = fmaf(-x, mp, B4.z);
-                        const float e2 = fmaf(-y, mp, B4.w);
-                        const float re = fmaf(e1, e1, -e2 * e2);
-                        const float im2 = e1 * e2;
-                        if (MODE == kForward) {
-                            const float al = fmaf(re, qp, -2.f * im2 * up);
-                            const float be = fmaf(2.f * im2, qp, re * up);
-                            acc[i] = fmaf(bA, ip, fmaf(bB, al, fmaf(bC, be, acc[i])));
-                        } else {
-                            const float yv = sY[i];
-                            gI = fmaf(yv, bA, gI);
-                            gQ = fmaf(yv, fmaf(bB, re, 2.f * bC * im2), gQ);
-                            gU = fmaf(yv, fmaf(bC, re, -2.f * bB * im2), gU);
+                        const float k0 = B4.y * sr2;   // 2 sin(theta0) sin(theta_r)
+                        const float k1 = -B4.x * sr2;  // -2 cos(theta0) sin(theta_r)
+#pragma unroll
+                        for (int p4 = 0; p4 < NP; ++p4) {
+                            if (!ok[p4]) continue;
+                            const float sh = fmaf(sa[p4], A4.x, -ca[p4] * A4.y);  // sin(dphi / 2)
+                            const float ch = fmaf(ca[p4], A4.x, sa[p4] * A4.y);   // cos(dphi / 2)
+                            const float sh2 = sh * sh;
+                            const float w = fmaf(k0, sh2, pa.y);  // 1 - k . p0
+                            if (w > P.wr_hi) continue;
+                            if (w > P.wr_lo &&
+                                !exact_in_disc(P.rings, c0 + ri, jw[p4], sPx[i], sPy[i], sPz[i], P.cos_r))
+                                continue;
+                            if (MODE == kCount) {
+                                acc[i] += 1.f;
+                                continue;
+                            }
+                            const float x0 = fmaf(k1, sh2, pa.x);
+                            const float y0 = sr2 * sh * ch;
+                            const float x = fmaf(A4.z, x0, A4.w * y0);   // k . theta'0
+                            const float y = fmaf(A4.z, y0, -A4.w * x0);  // k . phi'0
+                            const float fu = fmaf(x, P.invh_f, P.cg_f);
+                            const float fv = fmaf(y, P.invh_f, P.cg_f);
+                            const float flu = fminf(fmaxf(floorf(fu), 0.f), gmax);
+                            const float flv = fminf(fmaxf(floorf(fv), 0.f), gmax);
+                            const float fx = fmaf(x, P.invh_f, P.cg_f - flu);
+                            const float fy = fmaf(y, P.invh_f, P.cg_f - flv);
+                            float bA, bB, bC;
+                            if (FETCH == PISCO_FETCH_CELLS) {
+                                const int cell = (int)flv * nc + (int)flu;
+                                // consecutive samples of a pixel often fall in the cell of
+                                // the previous one: keep its coefficients in registers
+                                if (cell != lastcell[p4]) {
+                                    ld_nc_v8(cells + 16 * cell, cka[p4], ckb[p4]);
+                                    ckc[p4] = ld_nc_v4(cells + 16 * cell + 8);
+                                    lastcell[p4] = cell;
+                                }
+                                const float4 ka = cka[p4], kb = ckb[p4], kc = ckc[p4];
+                                bA = fmaf(fy, fmaf(fx, ka.w, ka.z), fmaf(fx, ka.y, ka.x));
+                                bB = fmaf(fy, fmaf(fx, kb.w, kb.z), fmaf(fx, kb.y, kb.x));
+                                bC = fmaf(fy, fmaf(fx, kc.w, kc.z), fmaf(fx, kc.y, kc.x));
+                            } else {
+                                // texel centres sit at integer + 1/2: (flu + 1, flv + 1) selects
+                                // nodes flu, flu + 1 and flv, flv + 1 exactly
+                                const float xc = flu + 1.f, yc = flv + 1.f;
+                                bA = lerp_gather(tex2Dgather<float4>(det.tex[0], xc, yc, 0), fx, fy);
+                                bB = lerp_gather(tex2Dgather<float4>(det.tex[1], xc, yc, 0), fx, fy);
+                                bC = lerp_gather(tex2Dgather<float4>(det.tex[2], xc, yc, 0), fx, fy);
+                            }
+                            const float q = rcp_approx(2.f - w);  // 1 / (1 + k . p0)
+                            const float mp = fmaf(q, fmaf(x, B4.z, y * B4.w), B4.x);
+                            const float e1 = fmaf(-x, mp, B4.z);
+                            const float e2 = fmaf(-y, mp, B4.w);
+                            const float re = fmaf(e1, e1, -e2 * e2);
+                            const float im2 = e1 * e2;
+                            if (MODE == kForward) {
+                                const float al = fmaf(re, qp[p4], -2.f * im2 * up[p4]);
+                                const float be = fmaf(2.f * im2, qp[p4], re * up[p4]);
+                                acc[i] = fmaf(bA, ip[p4], fmaf(bB, al, fmaf(bC, be, acc[i])));
+                            } else {
+                                const float yv = sY[i];
+                                gI[p4] = fmaf(yv, bA, gI[p4]);
+                                gQ[p4] = fmaf(yv, fmaf(bB, re, 2.f * bC * im2), gQ[p4]);
+                                gU[p4] = fmaf(yv, fmaf(bC, re, -2.f * bB * im2), gU[p4]);
+                            }
                         }
                     }
                     if (MODE == kAdjoint) {
-                        if (gI != 0.f || gQ != 0.f || gU != 0.f) {
-                            float* maps = (float*)P.out;
-                            atomicAdd(maps + pix, gI);
-                            atomicAdd(maps + P.npix + pix, gQ * inv);
-                            atomicAdd(maps + 2 * P.npix + pix, gU * inv);
+                        float* maps = (float*)P.out;
+#pragma unroll
+                        for (int p4 = 0; p4 < NP; ++p4) {
+                            if (ok[p4] && (gI[p4] != 0.f || gQ[p4] != 0.f || gU[p4] != 0.f)) {
+                                const long long pix = (long long)first + jw[p4];
+                                atomicAdd(maps + pix, gI[p4]);
+                                atomicAdd(maps + P.npix + pix, gQ[p4] * inv);
+                                atomicAdd(maps + 2 * P.npix + pix, gU[p4] * inv);
+                            }
                         }
                     }
                 }
@@ -395,23 +474,26 @@ __global__ void __launch_bounds__(NT, 2) k_fast(const __grid_constant__ LaunchPa
     }
 }
 
-template <int S>
+template <int S, int NP, int FETCH>
 static cudaError_t launch_s(const LaunchParams& p, int mode, cudaStream_t s) {
     if (p.total_tiles <= 0) return cudaSuccess;
     const unsigned grid = (unsigned)min(p.total_tiles, (long long)INT_MAX);
     switch (mode) {
-        case kForward: k_fast<S, kForward><<<grid, NT, 0, s>>>(p); break;
-        case kAdjoint: k_fast<S, kAdjoint><<<grid, NT, 0, s>>>(p); break;
-        default: k_fast<S, kCount><<<grid, NT, 0, s>>>(p); break;
+        case kForward: k_fast<S, NP, FETCH, kForward><<<grid, NT, 0, s>>>(p); break;
+        case kAdjoint: k_fast<S, NP, FETCH, kAdjoint><<<grid, NT, 0, s>>>(p); break;
+        default: k_fast<S, NP, FETCH, kCount><<<grid, NT, 0, s>>>(p); break;
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_fast(const LaunchParams& p, int mode, int tile_samples, cudaStream_t s) {
+// Dispatch over the tile size and pixels per thread for one fetch mode.
+template <int FETCH>
+static cudaError_t launch_fetch(const LaunchParams& p, int mode, int tile_samples, int np, cudaStream_t s) {
+    const bool one = np == 1;
     switch (tile_samples) {
-        case 8: return launch_s<8>(p, mode, s);
-        case 32: return launch_s<32>(p, mode, s);
-        default: return launch_s<16>(p, mode, s);
+        case 8: return one ? launch_s<8, 1, FETCH>(p, mode, s) : launch_s<8, 2, FETCH>(p, mode, s);
+        case 32: return one ? launch_s<32, 1, FETCH>(p, mode, s) : launch_s<32, 2, FETCH>(p, mode, s);
+        default: return one ? launch_s<16, 1, FETCH>(p, mode, s) : launch_s<16, 2, FETCH>(p, mode, s);
     }
 }
 

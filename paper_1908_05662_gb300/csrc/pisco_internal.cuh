@@ -32,8 +32,9 @@ struct DetEntry {
     long long begin;       // first sample, index into the pointing arrays
     long long count;       // number of samples
     long long tile_begin;  // first tile (block) index of this detector
-    const void* beam;      // FP32: float4 cells [(N-1)^2][3]; FP64: double nodes [3][N][N]
+    const void* beam;      // FP32: 64-byte cells [(N-1)^2][16 floats]; FP64: double nodes [3][N][N]
     double scale;          // (s/2) Omega_pix / Omega~
+    cudaTextureObject_t tex[3];  // FP32 texture fetch: folded node maps A, Bq', Cu' as 2-D float textures
 };
 
 constexpr int kMaxDetPerLaunch = 64;
@@ -76,6 +77,8 @@ struct pisco_plan {
     int grid_n;
     int precision;
     int tile_samples;
+    int pixels_per_thread;
+    int beam_fetch;    // PISCO_FETCH_CELLS or PISCO_FETCH_TEXTURE
     double radius;
     double cos_r;
     double omega_pix;
@@ -83,6 +86,8 @@ struct pisco_plan {
     void* d_sky;       // float4 [npix] or double [3][npix]
     void* d_beam;      // per detector FP32 cells or FP64 nodes, contiguous
     size_t beam_stride;  // bytes per detector in d_beam
+    cudaArray_t* h_arrays;           // [n_det][3] texture fetch: folded node maps
+    cudaTextureObject_t* h_tex;      // [n_det][3]
     double* h_omega;
     double* h_scale;
     pisco_detector* h_dets;
@@ -98,10 +103,12 @@ struct pisco_plan {
 namespace pisco {
 
 // Launchers (defined in the kernel translation units).
-cudaError_t launch_fast(const LaunchParams& p, int mode, int tile_samples, cudaStream_t s);
+cudaError_t launch_fast_texture(const LaunchParams& p, int mode, int tile_samples, int np, cudaStream_t s);
+cudaError_t launch_fast_cells(const LaunchParams& p, int mode, int tile_samples, int np, cudaStream_t s);
 cudaError_t launch_plain(const LaunchParams& p, int mode, cudaStream_t s);
 cudaError_t launch_plan_kernels(pisco_plan* plan, const void* sky, int sky_dtype,
                                 const float* grids, cudaStream_t s, double* d_omega_out);
+cudaError_t launch_fold_nodes32(const float* grids, int n, double eps, double zeta, float* out3, cudaStream_t s);
 
 void set_error(pisco_plan* plan, const char* fmt, ...);
 

@@ -14,8 +14,11 @@
 //    only through exp(2 i zeta), folded in as Bq' + i Cu' = (Bq + i Cu) e^{2 i zeta}.
 //    Bilinear interpolation is linear, so folding before interpolating is exact.
 //    FP32 plans store each grid cell as its bilinear coefficients
-//    f(fx, fy) = c0 + c1 fx + c2 fy + c3 fx fy for the three maps (48 bytes);
+//    f(fx, fy) = c0 + c1 fx + c2 fy + c3 fx fy for the three maps, padded to
+//    64 bytes so a cell spans two 32-byte sectors;
 //    plain plans keep the folded node values in float64;
+//    FP32 plans may instead keep the folded node values as three 2-D float
+//    textures, fetched with 2 x 2 gathers;
 //  * Omega~ = int B_TT dOmega (Sec. 3) by the trapezoid rule over the grid with
 //    the orthographic area element du dv / sqrt(1 - u^2 - v^2).
 
@@ -107,12 +110,13 @@ __global__ void k_cells(const float* __restrict__ g, int n, double eps, double z
     Folded f10 = fold_node(g, nn, (long long)j * n + i + 1, eps, c2z, s2z);
     Folded f01 = fold_node(g, nn, (long long)(j + 1) * n + i, eps, c2z, s2z);
     Folded f11 = fold_node(g, nn, (long long)(j + 1) * n + i + 1, eps, c2z, s2z);
-    cells[3 * cell + 0] = make_float4((float)f00.a, (float)(f10.a - f00.a), (float)(f01.a - f00.a),
+    cells[4 * cell + 0] = make_float4((float)f00.a, (float)(f10.a - f00.a), (float)(f01.a - f00.a),
                                       (float)(f11.a - f10.a - f01.a + f00.a));
-    cells[3 * cell + 1] = make_float4((float)f00.b, (float)(f10.b - f00.b), (float)(f01.b - f00.b),
+    cells[4 * cell + 1] = make_float4((float)f00.b, (float)(f10.b - f00.b), (float)(f01.b - f00.b),
                                       (float)(f11.b - f10.b - f01.b + f00.b));
-    cells[3 * cell + 2] = make_float4((float)f00.c, (float)(f10.c - f00.c), (float)(f01.c - f00.c),
+    cells[4 * cell + 2] = make_float4((float)f00.c, (float)(f10.c - f00.c), (float)(f01.c - f00.c),
                                       (float)(f11.c - f10.c - f01.c + f00.c));
+    cells[4 * cell + 3] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 __global__ void k_nodes64(const float* __restrict__ g, int n, double eps, double zeta,
@@ -126,6 +130,18 @@ __global__ void k_nodes64(const float* __restrict__ g, int n, double eps, double
     nodes[idx] = f.a;
     nodes[nn + idx] = f.b;
     nodes[2 * nn + idx] = f.c;
+}
+
+__global__ void k_nodes32(const float* __restrict__ g, int n, double eps, double zeta, float* __restrict__ out) {
+    const long long nn = (long long)n * n;
+    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= nn) return;
+    double s2z, c2z;
+    sincos(2.0 * zeta, &s2z, &c2z);
+    Folded f = fold_node(g, nn, idx, eps, c2z, s2z);
+    out[idx] = (float)f.a;
+    out[nn + idx] = (float)f.b;
+    out[2 * nn + idx] = (float)f.c;
 }
 
 // One block; fixed per-thread order and a fixed tree, so the result is deterministic.
@@ -152,6 +168,11 @@ __global__ void k_omega(const float* __restrict__ tt, int n, double sin_r, doubl
 
 static inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
+cudaError_t launch_fold_nodes32(const float* grids, int n, double eps, double zeta, float* out3, cudaStream_t s) {
+    k_nodes32<<<blocks_for((long long)n * n, 256), 256, 0, s>>>(grids, n, eps, zeta, out3);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_plan_kernels(pisco_plan* plan, const void* sky, int sky_dtype, const float* grids,
                                 cudaStream_t s, double* d_omega_out) {
     k_rings<<<blocks_for(plan->nrings, 128), 128, 0, s>>>(plan->nside, plan->nrings, plan->d_rings);
@@ -174,8 +195,10 @@ cudaError_t launch_plan_kernels(pisco_plan* plan, const void* sky, int sky_dtype
         char* dst = (char*)plan->d_beam + (size_t)d * plan->beam_stride;
         const pisco_detector& det = plan->h_dets[d];
         if (plan->precision == PISCO_FP32) {
-            const long long nc = (long long)(n - 1) * (n - 1);
-            k_cells<<<blocks_for(nc, 256), 256, 0, s>>>(g, n, det.eps, det.zeta, (float4*)dst);
+            if (plan->beam_fetch == PISCO_FETCH_CELLS) {
+                const long long nc = (long long)(n - 1) * (n - 1);
+                k_cells<<<blocks_for(nc, 256), 256, 0, s>>>(g, n, det.eps, det.zeta, (float4*)dst);
+            }
         } else {
             k_nodes64<<<blocks_for(nn, 256), 256, 0, s>>>(g, n, det.eps, det.zeta, (double*)dst);
         }

@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libpisco.so
 PISCO_OK, PISCO_EINVAL, PISCO_ENOMEM, PISCO_ECUDA, PISCO_ETIMEOUT, PISCO_EUNSUPPORTED, PISCO_EDEVICE = range(7)
 PISCO_FP64_PLAIN, PISCO_FP32 = 0, 1
 PISCO_DTYPE_F32, PISCO_DTYPE_F64 = 0, 1
+PISCO_FETCH_TEXTURE, PISCO_FETCH_CELLS = 1, 2
 
 STATUS_NAMES = {0: "PISCO_OK", 1: "PISCO_EINVAL", 2: "PISCO_ENOMEM", 3: "PISCO_ECUDA",
                 4: "PISCO_ETIMEOUT", 5: "PISCO_EUNSUPPORTED", 6: "PISCO_EDEVICE"}
@@ -39,7 +40,7 @@ class pisco_detector(ctypes.Structure):
 
 class pisco_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("tile_samples", ctypes.c_int),
-                ("reserved0", ctypes.c_int), ("reserved1", ctypes.c_int)]
+                ("pixels_per_thread", ctypes.c_int), ("beam_fetch", ctypes.c_int)]
 
 
 _lib = None
@@ -97,7 +98,7 @@ def _f64(t):
 
 
 def pisco_plan_create(nside, radius, sky, dets, beam_grids, omega_tilde=None,
-                      precision=PISCO_FP32, tile_samples=0):
+                      precision=PISCO_FP32, tile_samples=0, pixels_per_thread=0, beam_fetch=0):
     """Create a plan; returns an opaque handle (int).  sky: (3, 12 nside^2) CUDA tensor
     (float32 or float64); dets: list of (zeta, eps, s_resp); beam_grids: (n_det, 6, N, N)
     float32 CUDA tensor."""
@@ -115,7 +116,7 @@ def pisco_plan_create(nside, radius, sky, dets, beam_grids, omega_tilde=None,
         raise ValueError("sky must have shape (3, 12 nside^2)")
     arr = (pisco_detector * n_det)(*[pisco_detector(*map(float, d)) for d in dets])
     om = None if omega_tilde is None else (ctypes.c_double * n_det)(*map(float, omega_tilde))
-    opt = pisco_options(precision, tile_samples, 0, 0)
+    opt = pisco_options(precision, tile_samples, pixels_per_thread, beam_fetch)
     handle = ctypes.c_void_p()
     st = lib.pisco_plan_create(ctypes.byref(handle), int(nside), float(radius), _ptr(sky),
                                PISCO_DTYPE_F64 if sky.dtype == torch.float64 else PISCO_DTYPE_F32,
@@ -184,11 +185,11 @@ class Plan:
     """Owning wrapper: ``Plan(...)`` creates, ``close()`` / context exit destroys."""
 
     def __init__(self, nside, radius, sky, dets, beam_grids, omega_tilde=None, precision=PISCO_FP32,
-                 tile_samples=0):
+                 tile_samples=0, pixels_per_thread=0, beam_fetch=0):
         self.nside, self.radius, self.precision = nside, radius, precision
         self.n_det = len(dets)
         self.handle = pisco_plan_create(nside, radius, sky, dets, beam_grids, omega_tilde, precision,
-                                        tile_samples)
+                                        tile_samples, pixels_per_thread, beam_fetch)
 
     @property
     def out_dtype(self):

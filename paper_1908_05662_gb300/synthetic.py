@@ -99,20 +99,38 @@ def _synthesise(alms, nside, device):
         even += torch.where(sign_even[None, :, None], contrib, torch.zeros_like(contrib))
         odd += torch.where(sign_even[None, :, None], torch.zeros_like(contrib), contrib)
         prev2, prev1 = prev1, cur
+    # Each ring is a real Fourier series in phi: fold m into the ring's bins and
+    # inverse-FFT.  The 2 nside + 1 belt rings share one length and go in one batch.
+    cm = torch.where(m == 0, 1.0, 2.0).to(torch.complex128)
+    midx = torch.arange(lmax + 1, device=device)
+
+    def ring_coeffs(f, rows):
+        north = torch.tensor([r if r < nr else 4 * nside - 2 - r for r in rows], device=device)
+        sgn = torch.tensor([1.0 if r < nr else -1.0 for r in rows], dtype=torch.float64, device=device)
+        fm = even[f][:, north].T + sgn[:, None] * odd[f][:, north].T          # (rows, M)
+        phi0 = torch.tensor([layout[r][1] for r in rows], dtype=torch.float64, device=device)
+        return cm[None, :] * fm * torch.exp(1j * m[None, :] * phi0[:, None])
+
+    belt = list(range(nside - 1, 3 * nside))
     maps = []
     for f in range(nf):
-        rings = []
+        out = torch.empty(12 * nside * nside, dtype=torch.float64, device=device)
+        coef = ring_coeffs(f, belt)
+        folded = torch.zeros(len(belt), 4 * nside, dtype=torch.complex128, device=device)
+        folded.index_add_(1, midx % (4 * nside), coef)
+        vals = torch.real(torch.fft.ifft(folded, dim=1) * (4 * nside))
+        start = 2 * nside * (nside - 1)
+        out[start:start + vals.numel()] = vals.reshape(-1)
+        first = 0
         for r in range(4 * nside - 1):
-            zr, phi0, cnt = layout[r]
-            if r < nr:
-                fm = even[f, :, r] + odd[f, :, r]
-            else:
-                fm = even[f, :, 4 * nside - 2 - r] - odd[f, :, 4 * nside - 2 - r]
-            coef = torch.where(m == 0, 1.0, 2.0).to(torch.complex128) * fm * torch.exp(1j * m * phi0)
-            folded = torch.zeros(cnt, dtype=torch.complex128, device=device)
-            folded.index_add_(0, (torch.arange(lmax + 1, device=device) % cnt), coef)
-            rings.append(torch.real(torch.fft.ifft(folded) * cnt))
-        maps.append(torch.cat(rings))
+            cnt = layout[r][2]
+            if not (nside - 1 <= r < 3 * nside):
+                c = ring_coeffs(f, [r])[0]
+                folded = torch.zeros(cnt, dtype=torch.complex128, device=device)
+                folded.index_add_(0, midx % cnt, c)
+                out[first:first + cnt] = torch.real(torch.fft.ifft(folded) * cnt)
+            first += cnt
+        maps.append(out)
     return torch.stack(maps)
 
 

@@ -47,11 +47,12 @@ def _oracle(nside, radius, sky, grids, det, theta, phi, psi, omega=None):
     return d, mag
 
 
-def _gpu(nside, radius, sky, grids, dets, theta, phi, psi, precision, tile=0, det=0):
+def _gpu(nside, radius, sky, grids, dets, theta, phi, psi, precision, tile=0, det=0, np_=0):
     g = torch.as_tensor(np.asarray(grids, np.float32), device=DEV)
     if g.dim() == 3:
         g = g[None]
-    with pisco.Plan(nside, radius, _t(sky), dets, g.contiguous(), precision=precision, tile_samples=tile) as plan:
+    with pisco.Plan(nside, radius, _t(sky), dets, g.contiguous(), precision=precision, tile_samples=tile,
+                    pixels_per_thread=np_) as plan:
         out = plan.convolve(_t(theta), _t(phi), _t(psi), det=det)
         torch.cuda.synchronize()
         plan.sync_status()
@@ -102,7 +103,8 @@ def test_forward_random_beams_random_pointings(precision, rel, nside, radius_deg
 
 
 @pytest.mark.parametrize("tile", [8, 16, 32])
-def test_fp32_scan_tiles_and_ragged_tail(tile):
+@pytest.mark.parametrize("np_", [1, 2])
+def test_fp32_scan_tiles_and_ragged_tail(tile, np_):
     """Consecutive scan samples share disc traversals; n is not a multiple of the tile."""
     nside, r = 64, math.radians(6.0)
     sky = sy.gaussian_sky(nside, 7).numpy()
@@ -112,7 +114,7 @@ def test_fp32_scan_tiles_and_ragged_tail(tile):
     det = (0.4, 0.02, 1.0)
     th, ph, ps = sy.raster_scan(301, center=(0.9, 4.0), half_size=math.radians(4.0), rows=6)
     ref, mag = _oracle(nside, r, sky, grids, det, th, ph, ps)
-    out = _gpu(nside, r, sky, grids, [det], th, ph, ps, pisco.PISCO_FP32, tile=tile)
+    out = _gpu(nside, r, sky, grids, [det], th, ph, ps, pisco.PISCO_FP32, tile=tile, np_=np_)
     np.testing.assert_array_less(np.abs(out - ref), 2e-6 * mag)
     assert np.max(np.abs(out - ref)) <= 1e-6 * np.max(np.abs(ref))
 
