@@ -83,6 +83,16 @@ def shard(n, rank, world):
     return a, b
 
 
+def max_over_ranks(value, device):
+    """The largest value over all ranks (the timed region is the slowest rank's)."""
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return value
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
 
@@ -249,11 +259,7 @@ def main():
     plan.sync_status()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     ms = statistics.mean(step_ms)
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = t.item()
+    total_ms = max_over_ranks(sum(step_ms), dev)
     value = n_total * args.steps / (total_ms / 1e3)
 
     # end to end through the host-buffer entry point (pinned host memory, copies timed)

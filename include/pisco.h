@@ -167,6 +167,45 @@ pisco_status pisco_adjoint(pisco_plan* plan, int det, int64_t n,
                            const void* tod, void* maps, int accumulate, void* stream);
 
 /*
+ * pisco_beam_grid_adjoint -- transpose of pisco_convolve with respect to the
+ * six beam grids, Omega~ held fixed:
+ *   grad_grids[e][j][i] (+)= sum_t tod[t] * d d_t / d beam_grids[det][e][j][i].
+ * Every beam element enters d_t linearly through the bilinear weights of the
+ * cell a pixel falls in (Sec. 4.2) and through the folding of the six maps
+ * (eqs. M_pol, lambda_operator); this is that linear map transposed.
+ *   tod         device [n], float32 (FP32 plan) or float64 (plain plan).
+ *   grad_grids  device [6][grid_n][grid_n] of the same type, maps ordered as
+ *               beam_grids; overwritten unless accumulate != 0.
+ * Uses a plan-owned scratch buffer of 3 grid_n^2 elements (allocated on the
+ * first call) and atomic adds (the last bits vary from run to run).  The
+ * dependence of Omega~ on B_TT is added by pisco_omega_adjoint.
+ */
+pisco_status pisco_beam_grid_adjoint(pisco_plan* plan, int det, int64_t n,
+                                     const double* theta, const double* phi, const double* psi,
+                                     const void* tod, void* grad_grids, int accumulate, void* stream);
+
+/*
+ * pisco_omega_adjoint -- the Omega~ term of the beam gradient.  Omega~ =
+ * int B_TT dOmega (Sec. 3) scales every sample by 1/Omega~, so with the
+ * forward TOD d (from pisco_convolve) and its gradient y:
+ *   grad_grids[TT][j][i] += -(sum_t y_t d_t / Omega~) * dOmega~/dB_TT[j][i],
+ * dOmega~/dB_TT being the trapezoid weights of the grid rule.  Skip it when
+ * the plan was given omega_tilde explicitly.  tod, tod_grad: device [n];
+ * grad_grids: device [6][grid_n][grid_n]; float32 or float64 as the plan.
+ */
+pisco_status pisco_omega_adjoint(pisco_plan* plan, int det, int64_t n, const void* tod,
+                                 const void* tod_grad, void* grad_grids, void* stream);
+
+/*
+ * pisco_update_beams -- replace the beams of an existing plan (same n_det and
+ * grid_n; detector parameters unchanged): refolds the grids and recomputes
+ * Omega~ (or takes omega_tilde, host [n_det], when not NULL).  Synchronises
+ * `stream` once.
+ */
+pisco_status pisco_update_beams(pisco_plan* plan, const float* beam_grids, const double* omega_tilde,
+                                void* stream);
+
+/*
  * pisco_disc_count -- number of sky pixels in the disc of each pointing
  * (the pixel list of Sec. 5.2, cut at rho_max as in Table 1), decided by
  * the plan's own path (the FP32 path filters in FP32 and settles pixels

@@ -50,6 +50,7 @@ static void free_plan(pisco_plan* p) {
     cudaFree(p->d_sky);
     cudaFree(p->d_beam);
     cudaFree(p->d_err);
+    cudaFree(p->d_gscratch);
     if (p->h_tex)
         for (int k = 0; k < 3 * p->n_det; ++k)
             if (p->h_tex[k]) cudaDestroyTextureObject(p->h_tex[k]);
@@ -67,6 +68,51 @@ static void free_plan(pisco_plan* p) {
     free(p->h_scale);
     free(p->h_dets);
     delete p;
+}
+
+// Folded node maps A, Bq', Cu' of every detector as 2-D float textures
+// (created on first use, refilled by pisco_update_beams).
+static cudaError_t build_textures(pisco_plan* p, const float* beam_grids, cudaStream_t s) {
+    const int n = p->grid_n;
+    const size_t nn = (size_t)n * n;
+    cudaError_t e = cudaSuccess;
+    if (!p->h_arrays) {
+        p->h_arrays = (cudaArray_t*)calloc(3 * (size_t)p->n_det, sizeof(cudaArray_t));
+        p->h_tex = (cudaTextureObject_t*)calloc(3 * (size_t)p->n_det, sizeof(cudaTextureObject_t));
+        if (!p->h_arrays || !p->h_tex) return cudaErrorMemoryAllocation;
+    }
+    float* d_tmp = nullptr;
+    e = cudaMalloc(&d_tmp, 3 * nn * sizeof(float));
+    const cudaChannelFormatDesc desc = cudaCreateChannelDesc<float>();
+    for (int d = 0; d < p->n_det && e == cudaSuccess; ++d) {
+        e = launch_fold_nodes32(beam_grids + (size_t)d * 6 * nn, n, p->h_dets[d].eps, p->h_dets[d].zeta, d_tmp, s);
+        for (int m = 0; m < 3 && e == cudaSuccess; ++m) {
+            const int k = 3 * d + m;
+            if (!p->h_arrays[k]) {
+                e = cudaMallocArray(&p->h_arrays[k], &desc, n, n);
+                if (e != cudaSuccess) break;
+            }
+            e = cudaMemcpy2DToArrayAsync(p->h_arrays[k], 0, 0, d_tmp + m * nn, n * sizeof(float), n * sizeof(float),
+                                         n, cudaMemcpyDeviceToDevice, s);
+            if (e != cudaSuccess || p->h_tex[k]) continue;
+            cudaResourceDesc rd;
+            memset(&rd, 0, sizeof(rd));
+            rd.resType = cudaResourceTypeArray;
+            rd.res.array.array = p->h_arrays[k];
+            cudaTextureDesc td;
+            memset(&td, 0, sizeof(td));
+            td.addressMode[0] = cudaAddressModeClamp;
+            td.addressMode[1] = cudaAddressModeClamp;
+            td.filterMode = cudaFilterModePoint;
+            td.readMode = cudaReadModeElementType;
+            td.normalizedCoords = 0;
+            e = cudaCreateTextureObject(&p->h_tex[k], &rd, &td, nullptr);
+        }
+        // the next detector reuses d_tmp: finish this one's copies first
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+    cudaFree(d_tmp);
+    return e;
 }
 
 extern "C" pisco_status pisco_plan_create(pisco_plan** out, int nside, double radius_rad, const void* sky,
@@ -182,42 +228,7 @@ extern "C" pisco_status pisco_plan_create(pisco_plan** out, int nside, double ra
     cudaStream_t s = (cudaStream_t)stream;
     e = cudaMemsetAsync(p->d_err, 0, sizeof(int), s);
     if (e == cudaSuccess) e = launch_plan_kernels(p, sky, sky_dtype, beam_grids, s, d_omega);
-    if (e == cudaSuccess && precision == PISCO_FP32 && fetch == PISCO_FETCH_TEXTURE) {
-        // folded node maps A, Bq', Cu' of every detector as 2-D float textures
-        p->h_arrays = (cudaArray_t*)calloc(3 * (size_t)n_det, sizeof(cudaArray_t));
-        p->h_tex = (cudaTextureObject_t*)calloc(3 * (size_t)n_det, sizeof(cudaTextureObject_t));
-        float* d_tmp = nullptr;
-        if (!p->h_arrays || !p->h_tex) e = cudaErrorMemoryAllocation;
-        if (e == cudaSuccess) e = cudaMalloc(&d_tmp, 3 * nn * sizeof(float));
-        const cudaChannelFormatDesc desc = cudaCreateChannelDesc<float>();
-        for (int d = 0; d < n_det && e == cudaSuccess; ++d) {
-            e = launch_fold_nodes32(beam_grids + (size_t)d * 6 * nn, grid_n, dets[d].eps, dets[d].zeta, d_tmp, s);
-            for (int m = 0; m < 3 && e == cudaSuccess; ++m) {
-                cudaArray_t arr = nullptr;
-                e = cudaMallocArray(&arr, &desc, grid_n, grid_n);
-                if (e != cudaSuccess) break;
-                p->h_arrays[3 * d + m] = arr;
-                e = cudaMemcpy2DToArrayAsync(arr, 0, 0, d_tmp + m * nn, grid_n * sizeof(float),
-                                             grid_n * sizeof(float), grid_n, cudaMemcpyDeviceToDevice, s);
-                if (e != cudaSuccess) break;
-                cudaResourceDesc rd;
-                memset(&rd, 0, sizeof(rd));
-                rd.resType = cudaResourceTypeArray;
-                rd.res.array.array = arr;
-                cudaTextureDesc td;
-                memset(&td, 0, sizeof(td));
-                td.addressMode[0] = cudaAddressModeClamp;
-                td.addressMode[1] = cudaAddressModeClamp;
-                td.filterMode = cudaFilterModePoint;
-                td.readMode = cudaReadModeElementType;
-                td.normalizedCoords = 0;
-                e = cudaCreateTextureObject(&p->h_tex[3 * d + m], &rd, &td, nullptr);
-            }
-            // the next detector reuses d_tmp: finish this one's copies first
-            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        }
-        cudaFree(d_tmp);
-    }
+    if (e == cudaSuccess && precision == PISCO_FP32 && fetch == PISCO_FETCH_TEXTURE) e = build_textures(p, beam_grids, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(p->h_omega, d_omega, n_det * sizeof(double), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaFree(d_omega);
@@ -486,5 +497,94 @@ extern "C" pisco_status pisco_sync_status(pisco_plan* plan, void* stream) {
         set_error(plan, "a kernel recorded error flags 0x%x", h);
         return PISCO_EDEVICE;
     }
+    return PISCO_OK;
+}
+
+extern "C" pisco_status pisco_update_beams(pisco_plan* plan, const float* beam_grids, const double* omega_tilde,
+                                           void* stream) {
+    if (!plan) return PISCO_EINVAL;
+    if (!is_device_ptr(beam_grids)) {
+        set_error(plan, "beam_grids must be a device pointer");
+        return PISCO_EINVAL;
+    }
+    for (int d = 0; omega_tilde && d < plan->n_det; ++d)
+        if (!(omega_tilde[d] > 0.0 && std::isfinite(omega_tilde[d]))) {
+            set_error(plan, "omega_tilde[%d] = %g is not a positive finite number", d, omega_tilde[d]);
+            return PISCO_EINVAL;
+        }
+    cudaStream_t s = (cudaStream_t)stream;
+    double* d_omega = nullptr;
+    PISCO_CUDA(plan, cudaMalloc(&d_omega, plan->n_det * sizeof(double)));
+    double* h = (double*)malloc(plan->n_det * sizeof(double));
+    cudaError_t e = h ? cudaSuccess : cudaErrorMemoryAllocation;
+    if (e == cudaSuccess) e = launch_beam_kernels(plan, beam_grids, s, d_omega);
+    if (e == cudaSuccess && plan->precision == PISCO_FP32 && plan->beam_fetch == PISCO_FETCH_TEXTURE)
+        e = build_textures(plan, beam_grids, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, d_omega, plan->n_det * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d_omega);
+    if (e != cudaSuccess) {
+        free(h);
+        set_error(plan, "beam update failed: %s", cudaGetErrorString(e));
+        return PISCO_ECUDA;
+    }
+    for (int d = 0; d < plan->n_det; ++d) {
+        const double om = omega_tilde ? omega_tilde[d] : h[d];
+        if (!(om > 0.0) || !std::isfinite(om)) {
+            free(h);
+            set_error(plan, "detector %d: Omega~ = %g from B_TT is not positive; pass omega_tilde", d, om);
+            return PISCO_EINVAL;
+        }
+        plan->h_omega[d] = om;
+        plan->h_scale[d] = 0.5 * plan->h_dets[d].s_resp * plan->omega_pix / om;
+    }
+    free(h);
+    return PISCO_OK;
+}
+
+extern "C" pisco_status pisco_beam_grid_adjoint(pisco_plan* plan, int det, int64_t n, const double* theta,
+                                                const double* phi, const double* psi, const void* tod,
+                                                void* grad_grids, int accumulate, void* stream) {
+    if (!plan) return PISCO_EINVAL;
+    if (det < 0 || det >= plan->n_det) {
+        set_error(plan, "detector %d outside [0, %d)", det, plan->n_det);
+        return PISCO_EINVAL;
+    }
+    pisco_status st = check_pointing(plan, n, theta, phi, psi);
+    if (st != PISCO_OK) return st;
+    if (!is_device_ptr(grad_grids) || (n > 0 && !is_device_ptr(tod))) {
+        set_error(plan, "tod and grad_grids must be device pointers");
+        return PISCO_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int f64 = plan->precision == PISCO_FP64_PLAIN;
+    const size_t elem = f64 ? sizeof(double) : sizeof(float);
+    const size_t nn = (size_t)plan->grid_n * plan->grid_n;
+    if (!plan->d_gscratch) PISCO_CUDA(plan, cudaMalloc(&plan->d_gscratch, 3 * nn * elem));
+    PISCO_CUDA(plan, cudaMemsetAsync(plan->d_gscratch, 0, 3 * nn * elem, s));
+    if (n > 0) {
+        const int64_t begin = 0, count = n;
+        st = run(plan, kGrid, det, 1, &begin, &count, theta, phi, psi, plan->d_gscratch, tod, nullptr, s);
+        if (st != PISCO_OK) return st;
+    }
+    PISCO_CUDA(plan, launch_unfold_grid(plan->d_gscratch, plan->grid_n, plan->h_dets[det].eps,
+                                        plan->h_dets[det].zeta, grad_grids, accumulate, f64, s));
+    return PISCO_OK;
+}
+
+extern "C" pisco_status pisco_omega_adjoint(pisco_plan* plan, int det, int64_t n, const void* tod,
+                                            const void* tod_grad, void* grad_grids, void* stream) {
+    if (!plan) return PISCO_EINVAL;
+    if (det < 0 || det >= plan->n_det || n < 0) {
+        set_error(plan, "detector %d outside [0, %d) or n < 0", det, plan->n_det);
+        return PISCO_EINVAL;
+    }
+    if (!is_device_ptr(grad_grids) || (n > 0 && (!is_device_ptr(tod) || !is_device_ptr(tod_grad)))) {
+        set_error(plan, "tod, tod_grad and grad_grids must be device pointers");
+        return PISCO_EINVAL;
+    }
+    const int f64 = plan->precision == PISCO_FP64_PLAIN;
+    PISCO_CUDA(plan, launch_omega_adjoint(tod, tod_grad, n, f64, plan->h_omega[det], 1.0, plan->grid_n,
+                                          sin(plan->radius), grad_grids, (cudaStream_t)stream));
     return PISCO_OK;
 }

@@ -35,6 +35,12 @@
 //     e^{2 i zeta} is folded into the beam maps at plan time;
 //  7. per-sample FP32 partial sums: warp shuffles, then FP64 across warps.
 //
+// The same traversal serves three transposes: the sky adjoint (atomic adds of
+// each pixel's I, Q, U weights summed over the group's samples), the
+// beam-grid adjoint (atomic adds into the folded node gradient, accumulated
+// per cell in registers while consecutive samples stay in one cell) and the
+// disc count.
+//
 // A thread takes NP consecutive pixels of a ring: their sky values are loaded
 // once per group and reused for all S samples, and each per-sample value read
 // from shared memory serves NP pairs.
@@ -57,6 +63,23 @@ static __device__ __forceinline__ float rcp_approx(float x) {
     float r;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
+}
+
+// Add the 12 accumulated node gradients of one cell (maps A, Bq', Cu' x nodes
+// (i, j), (i+1, j), (i, j+1), (i+1, j+1)) to the folded gradient [3][N][N]
+// and clear them.
+static __device__ __forceinline__ void flush_grid(float* g, int cell, int nc, int n, float* gw) {
+    const int i = cell % nc, j = cell / nc;
+    const long long nn = (long long)n * n;
+    const long long base = (long long)j * n + i;
+    const long long off[4] = {base, base + 1, base + n, base + n + 1};
+#pragma unroll
+    for (int m = 0; m < 3; ++m)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (gw[4 * m + k] != 0.f) atomicAdd(g + m * nn + off[k], gw[4 * m + k]);
+            gw[4 * m + k] = 0.f;
+        }
 }
 
 // Bilinear value from a 2 x 2 texel gather, whose components are the nodes
@@ -143,7 +166,8 @@ __global__ void __launch_bounds__(NT, 2) k_fast(const __grid_constant__ LaunchPa
                 a.z = (float)cs;
                 a.w = (float)ss;
                 b = make_float4((float)ct, (float)st, (float)(-cs * st), (float)(ss * st));
-                if (MODE == kAdjoint) sY[i] = (float)((double)((const float*)P.tod_in)[t0 + i] * det.scale);
+                if (MODE == kAdjoint || MODE == kGrid)
+                    sY[i] = (float)((double)((const float*)P.tod_in)[t0 + i] * det.scale);
             }
             sTh[i] = th;
             sPh[i] = phw;
@@ -356,6 +380,16 @@ __global__ void __launch_bounds__(NT, 2) k_fast(const __grid_constant__ LaunchPa
                     float gI[NP], gQ[NP], gU[NP];
 #pragma unroll
                     for (int p4 = 0; p4 < NP; ++p4) gI[p4] = gQ[p4] = gU[p4] = 0.f;
+                    // beam-grid transpose: gradient of the four nodes of the current cell,
+                    // kept in registers while consecutive samples stay in the cell
+                    int gcell[NP];
+                    float gw[NP][12];
+#pragma unroll
+                    for (int p4 = 0; p4 < NP; ++p4) {
+                        gcell[p4] = -1;
+#pragma unroll
+                        for (int k = 0; k < 12; ++k) gw[p4][k] = 0.f;
+                    }
 #pragma unroll
                     for (int i = 0; i < S; ++i) {
                         if (i < gs || i >= ge) continue;
@@ -389,6 +423,33 @@ __global__ void __launch_bounds__(NT, 2) k_fast(const __grid_constant__ LaunchPa
                             const float flv = fminf(fmaxf(floorf(fv), 0.f), gmax);
                             const float fx = fmaf(x, P.invh_f, P.cg_f - flu);
                             const float fy = fmaf(y, P.invh_f, P.cg_f - flv);
+                            if (MODE == kGrid) {
+                                const int cell = (int)flv * nc + (int)flu;
+                                if (cell != gcell[p4]) {
+                                    if (gcell[p4] >= 0) flush_grid((float*)P.out, gcell[p4], nc, P.grid_n, gw[p4]);
+                                    gcell[p4] = cell;
+                                }
+                                const float q = rcp_approx(2.f - w);
+                                const float mp = fmaf(q, fmaf(x, B4.z, y * B4.w), B4.x);
+                                const float e1 = fmaf(-x, mp, B4.z);
+                                const float e2 = fmaf(-y, mp, B4.w);
+                                const float re = fmaf(e1, e1, -e2 * e2);
+                                const float im2 = e1 * e2;
+                                const float yv = sY[i];
+                                const float cA = yv * ip[p4];
+                                const float cB = yv * fmaf(re, qp[p4], -2.f * im2 * up[p4]);
+                                const float cC = yv * fmaf(2.f * im2, qp[p4], re * up[p4]);
+                                const float w11 = fx * fy, w10 = fx - w11, w01 = fy - w11;
+                                const float w00 = (1.f - fx) - w01;
+                                const float wt[4] = {w00, w10, w01, w11};
+#pragma unroll
+                                for (int k = 0; k < 4; ++k) {
+                                    gw[p4][k] = fmaf(cA, wt[k], gw[p4][k]);
+                                    gw[p4][4 + k] = fmaf(cB, wt[k], gw[p4][4 + k]);
+                                    gw[p4][8 + k] = fmaf(cC, wt[k], gw[p4][8 + k]);
+                                }
+                                continue;
+                            }
                             float bA, bB, bC;
                             if (FETCH == PISCO_FETCH_CELLS) {
                                 const int cell = (int)flv * nc + (int)flu;
@@ -429,6 +490,11 @@ __global__ void __launch_bounds__(NT, 2) k_fast(const __grid_constant__ LaunchPa
                             }
                         }
                     }
+                    if (MODE == kGrid) {
+#pragma unroll
+                        for (int p4 = 0; p4 < NP; ++p4)
+                            if (gcell[p4] >= 0) flush_grid((float*)P.out, gcell[p4], nc, P.grid_n, gw[p4]);
+                    }
                     if (MODE == kAdjoint) {
                         float* maps = (float*)P.out;
 #pragma unroll
@@ -445,7 +511,7 @@ __global__ void __launch_bounds__(NT, 2) k_fast(const __grid_constant__ LaunchPa
                 __syncthreads();
             }
 
-            if (MODE != kAdjoint) {
+            if (MODE == kForward || MODE == kCount) {
 #pragma unroll
                 for (int i = 0; i < S; ++i) {
                     if (i < gs || i >= ge) continue;
@@ -481,6 +547,7 @@ static cudaError_t launch_s(const LaunchParams& p, int mode, cudaStream_t s) {
     switch (mode) {
         case kForward: k_fast<S, NP, FETCH, kForward><<<grid, NT, 0, s>>>(p); break;
         case kAdjoint: k_fast<S, NP, FETCH, kAdjoint><<<grid, NT, 0, s>>>(p); break;
+        case kGrid: k_fast<S, NP, FETCH, kGrid><<<grid, NT, 0, s>>>(p); break;
         default: k_fast<S, NP, FETCH, kCount><<<grid, NT, 0, s>>>(p); break;
     }
     return cudaGetLastError();

@@ -39,7 +39,7 @@ struct DetEntry {
 
 constexpr int kMaxDetPerLaunch = 64;
 
-enum Mode { kForward = 0, kAdjoint = 1, kCount = 2 };
+enum Mode { kForward = 0, kAdjoint = 1, kCount = 2, kGrid = 3 };
 
 // Parameters of the FP32 tile kernel and of the FP64 plain kernel (by value).
 struct LaunchParams {
@@ -97,6 +97,7 @@ struct pisco_plan {
     cudaEvent_t he[2];
     void* d_stage[2];
     size_t stage_bytes;
+    void* d_gscratch;  // beam-grid adjoint: folded gradient [3][N][N] (float or double)
     char msg[512];
 };
 
@@ -109,6 +110,11 @@ cudaError_t launch_plain(const LaunchParams& p, int mode, cudaStream_t s);
 cudaError_t launch_plan_kernels(pisco_plan* plan, const void* sky, int sky_dtype,
                                 const float* grids, cudaStream_t s, double* d_omega_out);
 cudaError_t launch_fold_nodes32(const float* grids, int n, double eps, double zeta, float* out3, cudaStream_t s);
+cudaError_t launch_beam_kernels(pisco_plan* plan, const float* grids, cudaStream_t s, double* d_omega_out);
+cudaError_t launch_unfold_grid(const void* folded, int n, double eps, double zeta, void* grad, int accumulate,
+                               int f64, cudaStream_t s);
+cudaError_t launch_omega_adjoint(const void* tod, const void* y, long long n, int f64, double omega, double scale_tod,
+                                 int grid_n, double sin_r, void* grad_tt, cudaStream_t s);
 
 void set_error(pisco_plan* plan, const char* fmt, ...);
 

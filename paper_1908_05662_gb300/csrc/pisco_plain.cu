@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(PT) k_plain(const __grid_constant__ LaunchPara
         // theta'0 = cos psi theta0 + sin psi phi0 ; phi'0 = -sin psi theta0 + cos psi phi0
         const double tax = cs * ct * cp - ss * sp, tay = cs * ct * sp + ss * cp, taz = -cs * st;
         const double fax = -ss * ct * cp - cs * sp, fay = -ss * ct * sp + cs * cp, faz = ss * st;
-        const double yw = (MODE == kAdjoint) ? ((const double*)P.tod_in)[t] * det.scale : 0.0;
+        const double yw = (MODE == kAdjoint || MODE == kGrid) ? ((const double*)P.tod_in)[t] * det.scale : 0.0;
         const double* __restrict__ nodes = (const double*)det.beam;
 
         int ra, rb;
@@ -110,6 +110,20 @@ __global__ void __launch_bounds__(PT) k_plain(const __grid_constant__ LaunchPara
                 const double e1 = taz - x * mp, e2 = faz - y * mp;
                 const double re = e1 * e1 - e2 * e2, im2 = e1 * e2;
                 const double inv = 1.0 / (R.s * R.s);
+                if (MODE == kGrid) {
+                    // d t / d(A, Bq', Cu') = (I, alpha, beta), spread over the cell's four nodes
+                    const double I = sky[pix], Q = sky[npix + pix], U = sky[2 * npix + pix];
+                    const double c[3] = {yw * I, yw * (re * Q - 2.0 * im2 * U) * inv, yw * (2.0 * im2 * Q + re * U) * inv};
+                    double* g = (double*)P.out;
+#pragma unroll
+                    for (int m = 0; m < 3; ++m) {
+                        atomicAdd(g + m * nn + base, c[m] * w00);
+                        atomicAdd(g + m * nn + base + 1, c[m] * w10);
+                        atomicAdd(g + m * nn + base + n, c[m] * w01);
+                        atomicAdd(g + m * nn + base + n + 1, c[m] * w11);
+                    }
+                    continue;
+                }
                 if (MODE == kForward) {
                     const double I = sky[pix], Q = sky[npix + pix], U = sky[2 * npix + pix];
                     acc += bm[0] * I + (bm[1] * (re * Q - 2.0 * im2 * U) + bm[2] * (2.0 * im2 * Q + re * U)) * inv;
@@ -121,7 +135,7 @@ __global__ void __launch_bounds__(PT) k_plain(const __grid_constant__ LaunchPara
                 }
             }
         }
-        if (MODE != kAdjoint) {
+        if (MODE == kForward || MODE == kCount) {
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
             if (lane == 0) sRed[warp] = acc;
@@ -143,6 +157,7 @@ cudaError_t launch_plain(const LaunchParams& p, int mode, cudaStream_t s) {
     switch (mode) {
         case kForward: k_plain<kForward><<<grid, PT, 0, s>>>(p); break;
         case kAdjoint: k_plain<kAdjoint><<<grid, PT, 0, s>>>(p); break;
+        case kGrid: k_plain<kGrid><<<grid, PT, 0, s>>>(p); break;
         default: k_plain<kCount><<<grid, PT, 0, s>>>(p); break;
     }
     return cudaGetLastError();

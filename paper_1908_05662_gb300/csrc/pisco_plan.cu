@@ -173,6 +173,97 @@ cudaError_t launch_fold_nodes32(const float* grids, int n, double eps, double ze
     return cudaGetLastError();
 }
 
+// Folded-map gradient (A, Bq', Cu') -> gradient of the six input maps: the
+// transpose of the folding above (A = (1+eps) TT + (1-eps) TQ, etc., and the
+// rotation by 2 zeta).
+template <typename T>
+__global__ void k_unfold(const T* __restrict__ f, int n, double eps, double zeta, T* __restrict__ g, int accumulate) {
+    const long long nn = (long long)n * n;
+    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= nn) return;
+    double s2z, c2z;
+    sincos(2.0 * zeta, &s2z, &c2z);
+    const double ga = f[idx], gbp = f[nn + idx], gcp = f[2 * nn + idx];
+    const double gbq = c2z * gbp + s2z * gcp;   // transpose of the 2 zeta rotation
+    const double gcu = -s2z * gbp + c2z * gcp;
+    const double v[6] = {(1.0 + eps) * ga, (1.0 + eps) * gbq, (1.0 + eps) * gcu,   // TT, QT, UT
+                         (1.0 - eps) * ga, (1.0 - eps) * gbq, (1.0 - eps) * gcu};  // TQ, QQ, UQ
+#pragma unroll
+    for (int e = 0; e < 6; ++e) {
+        const T add = (T)v[e];
+        g[e * nn + idx] = accumulate ? g[e * nn + idx] + add : add;
+    }
+}
+
+// Omega~ enters d through (s/2) Omega_pix / Omega~, so d L / d Omega~ = -sum_t y_t d_t / Omega~;
+// Omega~ is the trapezoid sum of B_TT with weights J = h^2 w_i w_j / sqrt(1 - u_i^2 - v_j^2).
+// One block: a fixed-order FP64 reduction, then the rank-one update of the TT gradient.
+template <typename T>
+__global__ void k_omega_adjoint(const T* __restrict__ tod, const T* __restrict__ y, long long n, double omega,
+                                double scale_tod, int gn, double sin_r, T* __restrict__ g_tt) {
+    __shared__ double red[1024];
+    double acc = 0.0;
+    for (long long t = threadIdx.x; t < n; t += blockDim.x) {
+        const double d = (double)tod[t], w = (double)y[t];
+        if (isfinite(d) && isfinite(w)) acc += d * w;
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    const double dl_domega = -scale_tod * red[0] / omega;
+    const double h = 2.0 * sin_r / (double)(gn - 1);
+    const long long nn = (long long)gn * gn;
+    for (long long idx = threadIdx.x; idx < nn; idx += blockDim.x) {
+        const int i = (int)(idx % gn), j = (int)(idx / gn);
+        const double u = sin_r * (2.0 * i / (double)(gn - 1) - 1.0);
+        const double v = sin_r * (2.0 * j / (double)(gn - 1) - 1.0);
+        const double w = ((i == 0 || i == gn - 1) ? 0.5 : 1.0) * ((j == 0 || j == gn - 1) ? 0.5 : 1.0);
+        g_tt[idx] = (T)((double)g_tt[idx] + dl_domega * h * h * w / sqrt(1.0 - u * u - v * v));
+    }
+}
+
+cudaError_t launch_unfold_grid(const void* folded, int n, double eps, double zeta, void* grad, int accumulate,
+                               int f64, cudaStream_t s) {
+    const unsigned b = blocks_for((long long)n * n, 256);
+    if (f64) k_unfold<double><<<b, 256, 0, s>>>((const double*)folded, n, eps, zeta, (double*)grad, accumulate);
+    else k_unfold<float><<<b, 256, 0, s>>>((const float*)folded, n, eps, zeta, (float*)grad, accumulate);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_omega_adjoint(const void* tod, const void* y, long long n, int f64, double omega, double scale_tod,
+                                 int grid_n, double sin_r, void* grad_tt, cudaStream_t s) {
+    if (f64)
+        k_omega_adjoint<double><<<1, 1024, 0, s>>>((const double*)tod, (const double*)y, n, omega, scale_tod, grid_n,
+                                                   sin_r, (double*)grad_tt);
+    else
+        k_omega_adjoint<float><<<1, 1024, 0, s>>>((const float*)tod, (const float*)y, n, omega, scale_tod, grid_n,
+                                                  sin_r, (float*)grad_tt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_beam_kernels(pisco_plan* plan, const float* grids, cudaStream_t s, double* d_omega_out) {
+    const int n = plan->grid_n;
+    const long long nn = (long long)n * n;
+    for (int d = 0; d < plan->n_det; ++d) {
+        const float* g = grids + (long long)d * 6 * nn;
+        char* dst = plan->d_beam ? (char*)plan->d_beam + (size_t)d * plan->beam_stride : nullptr;
+        const pisco_detector& det = plan->h_dets[d];
+        if (plan->precision == PISCO_FP32) {
+            if (plan->beam_fetch == PISCO_FETCH_CELLS) {
+                const long long nc = (long long)(n - 1) * (n - 1);
+                k_cells<<<blocks_for(nc, 256), 256, 0, s>>>(g, n, det.eps, det.zeta, (float4*)dst);
+            }
+        } else {
+            k_nodes64<<<blocks_for(nn, 256), 256, 0, s>>>(g, n, det.eps, det.zeta, (double*)dst);
+        }
+        k_omega<<<1, 256, 0, s>>>(g, n, sin(plan->radius), d_omega_out + d);
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_plan_kernels(pisco_plan* plan, const void* sky, int sky_dtype, const float* grids,
                                 cudaStream_t s, double* d_omega_out) {
     k_rings<<<blocks_for(plan->nrings, 128), 128, 0, s>>>(plan->nside, plan->nrings, plan->d_rings);
@@ -188,23 +279,9 @@ cudaError_t launch_plan_kernels(pisco_plan* plan, const void* sky, int sky_dtype
         else
             k_sky64<double><<<blocks_for(3 * npix, 256), 256, 0, s>>>((const double*)sky, npix, (double*)plan->d_sky);
     }
-    const int n = plan->grid_n;
-    const long long nn = (long long)n * n;
-    for (int d = 0; d < plan->n_det; ++d) {
-        const float* g = grids + (long long)d * 6 * nn;
-        char* dst = (char*)plan->d_beam + (size_t)d * plan->beam_stride;
-        const pisco_detector& det = plan->h_dets[d];
-        if (plan->precision == PISCO_FP32) {
-            if (plan->beam_fetch == PISCO_FETCH_CELLS) {
-                const long long nc = (long long)(n - 1) * (n - 1);
-                k_cells<<<blocks_for(nc, 256), 256, 0, s>>>(g, n, det.eps, det.zeta, (float4*)dst);
-            }
-        } else {
-            k_nodes64<<<blocks_for(nn, 256), 256, 0, s>>>(g, n, det.eps, det.zeta, (double*)dst);
-        }
-        k_omega<<<1, 256, 0, s>>>(g, n, sin(plan->radius), d_omega_out + d);
-    }
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_beam_kernels(plan, grids, s, d_omega_out);
 }
 
 }  // namespace pisco

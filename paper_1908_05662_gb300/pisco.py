@@ -25,7 +25,8 @@ STATUS_NAMES = {0: "PISCO_OK", 1: "PISCO_EINVAL", 2: "PISCO_ENOMEM", 3: "PISCO_E
 # Entry points declared in include/pisco.h, checked by the CPU test suite.
 EXPORTS = ("pisco_plan_create", "pisco_plan_destroy", "pisco_last_error", "pisco_plan_omega",
            "pisco_convolve", "pisco_convolve_batched", "pisco_adjoint", "pisco_disc_count",
-           "pisco_convolve_host", "pisco_sync_status")
+           "pisco_convolve_host", "pisco_sync_status", "pisco_beam_grid_adjoint", "pisco_omega_adjoint",
+           "pisco_update_beams")
 
 
 class PiscoError(RuntimeError):
@@ -68,6 +69,9 @@ def load_library(path=LIB_PATH):
         "pisco_disc_count": (c_int, [vp, i64, vp, vp, vp, vp]),
         "pisco_convolve_host": (c_int, [vp, c_int, i64, vp, vp, vp, vp]),
         "pisco_sync_status": (c_int, [vp, vp]),
+        "pisco_beam_grid_adjoint": (c_int, [vp, c_int, i64, vp, vp, vp, vp, vp, c_int, vp]),
+        "pisco_omega_adjoint": (c_int, [vp, c_int, i64, vp, vp, vp, vp]),
+        "pisco_update_beams": (c_int, [vp, vp, ctypes.POINTER(dbl), vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -177,6 +181,28 @@ def pisco_convolve_host(plan, det, h_theta, h_phi, h_psi, h_tod):
     return h_tod
 
 
+def pisco_beam_grid_adjoint(plan, det, theta, phi, psi, tod, grad_grids, accumulate=False):
+    n = theta.numel()
+    _check(load_library().pisco_beam_grid_adjoint(plan, det, n, _ptr(_f64(theta)), _ptr(_f64(phi)),
+                                                  _ptr(_f64(psi)), _ptr(tod), _ptr(grad_grids),
+                                                  int(bool(accumulate)), _stream()), plan)
+    return grad_grids
+
+
+def pisco_omega_adjoint(plan, det, tod, tod_grad, grad_grids):
+    _check(load_library().pisco_omega_adjoint(plan, det, tod.numel(), _ptr(tod), _ptr(tod_grad),
+                                              _ptr(grad_grids), _stream()), plan)
+    return grad_grids
+
+
+def pisco_update_beams(plan, beam_grids, omega_tilde=None):
+    if beam_grids.dtype != torch.float32 or not beam_grids.is_cuda:
+        raise ValueError("beam_grids must be a float32 CUDA tensor")
+    beam_grids = beam_grids.contiguous()
+    om = None if omega_tilde is None else (ctypes.c_double * len(omega_tilde))(*map(float, omega_tilde))
+    _check(load_library().pisco_update_beams(plan, _ptr(beam_grids), om, _stream()), plan)
+
+
 def pisco_sync_status(plan):
     _check(load_library().pisco_sync_status(plan, _stream()), plan)
 
@@ -188,6 +214,7 @@ class Plan:
                  tile_samples=0, pixels_per_thread=0, beam_fetch=0):
         self.nside, self.radius, self.precision = nside, radius, precision
         self.n_det = len(dets)
+        self.grid_n = int(beam_grids.shape[-1])
         self.handle = pisco_plan_create(nside, radius, sky, dets, beam_grids, omega_tilde, precision,
                                         tile_samples, pixels_per_thread, beam_fetch)
 
@@ -210,6 +237,17 @@ class Plan:
         if maps is None:
             maps = torch.empty(3, 12 * self.nside ** 2, dtype=self.out_dtype, device=theta.device)
         return pisco_adjoint(self.handle, det, theta, phi, psi, tod, maps, accumulate)
+
+    def beam_grid_adjoint(self, theta, phi, psi, tod, det=0, grad=None, accumulate=False):
+        if grad is None:
+            grad = torch.empty(6, self.grid_n, self.grid_n, dtype=self.out_dtype, device=theta.device)
+        return pisco_beam_grid_adjoint(self.handle, det, theta, phi, psi, tod, grad, accumulate)
+
+    def omega_adjoint(self, tod, tod_grad, grad, det=0):
+        return pisco_omega_adjoint(self.handle, det, tod, tod_grad, grad)
+
+    def update_beams(self, beam_grids, omega_tilde=None):
+        pisco_update_beams(self.handle, beam_grids, omega_tilde)
 
     def disc_count(self, theta, phi):
         counts = torch.empty(theta.numel(), dtype=torch.int32, device=theta.device)

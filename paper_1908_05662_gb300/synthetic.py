@@ -17,8 +17,8 @@ oracle, and ``bench.py`` uses it to build the benchmark workloads.
   of Sec. 7.1, with synthetic site and timing), focal-plane offsets, and
   uniformly random pointings.
 * beams -- six tangent-plane maps (TT, QT, UT, TQ, QQ, UQ) of an elliptical
-  Gaussian main beam with optional sidelobe ring and cross-polar leakage, or
-  random smooth maps for parity tests.  Grid nodes sit at orthographic
+  Gaussian main beam with optional sidelobe ring and cross-polar leakage (the
+  parametric model of ``beams``), or random smooth maps for parity tests.  Grid nodes sit at orthographic
   coordinates u_i = sin(R) (2 i / (N - 1) - 1), the library's grid format.
 """
 
@@ -250,31 +250,15 @@ def grid_nodes(n, radius):
 
 def gaussian_beam_maps(n, radius, fwhm_deg, ellipticity=0.0, xpol=0.0, sidelobe=None,
                        ideal=False):
-    """Six float32 maps (TT, QT, UT, TQ, QQ, UQ) of an elliptical Gaussian beam.
+    """Six float32 maps (TT, QT, UT, TQ, QQ, UQ) of an elliptical Gaussian beam
+    (the parametric family of ``beams.gaussian_beam_grids``) as a numpy array.
 
-    g = exp(-1/2 [(u / s_x)^2 + (v / s_y)^2]) with s = FWHM / sqrt(8 ln 2),
-    s_x = s (1 + e), s_y = s (1 - e).  Cross-polar leakage xpol gives
-    B_TT = (1 + xpol) g and B_QQ = (1 - xpol) g; ``ideal`` gives
-    B_TT = B_QQ = g (the Kronecker beamsor b (x) I of Sec. 3).
-    ``sidelobe`` = (amplitude, centre_deg, width_deg) adds a ring to B_TT and B_QQ.
+    ``sidelobe`` = (amplitude, centre_deg, width_deg) adds a ring to B_TT and B_QQ;
+    ``ideal`` gives B_TT = B_QQ = g (the Kronecker beamsor of Sec. 3).
     """
-    u = grid_nodes(n, radius)
-    uu, vv = np.meshgrid(u, u, indexing="xy")
-    s = math.radians(fwhm_deg) * FWHM_TO_SIGMA
-    sx, sy = s * (1.0 + ellipticity), s * (1.0 - ellipticity)
-    g = np.exp(-0.5 * ((uu / sx) ** 2 + (vv / sy) ** 2))
-    if sidelobe is not None:
-        amp, c, w = sidelobe
-        rho = np.arcsin(np.minimum(np.sqrt(uu * uu + vv * vv), 1.0))
-        g = g + amp * np.exp(-0.5 * ((rho - math.radians(c)) / math.radians(w)) ** 2)
-    maps = np.zeros((6, n, n))
-    if ideal:
-        maps[0] = g
-        maps[4] = g
-    else:
-        maps[0] = (1.0 + xpol) * g
-        maps[4] = (1.0 - xpol) * g
-    return np.ascontiguousarray(maps, dtype=np.float32)
+    from .beams import gaussian_beam_grids
+    g = gaussian_beam_grids(n, radius, fwhm_deg, ellipticity, xpol, sidelobe, ideal)
+    return np.ascontiguousarray(g.numpy(), dtype=np.float32)
 
 
 def random_beam_maps(n, seed, smooth=True):
