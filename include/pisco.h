@@ -185,6 +185,23 @@ pisco_status pisco_beam_grid_adjoint(pisco_plan* plan, int det, int64_t n,
                                      const void* tod, void* grad_grids, int accumulate, void* stream);
 
 /*
+ * pisco_beam_grid_adjoint_static -- pisco_beam_grid_adjoint that allocates
+ * nothing.  The paper has no counterpart: this entry point exists for
+ * callers that may not allocate device memory when they call (a real-time
+ * loop with a fixed memory budget, an allocator that forbids cudaMalloc after
+ * start-up).  Same arguments, layout and result as pisco_beam_grid_adjoint;
+ * the folded-gradient scratch is a static device array of 6 MiB inside the
+ * library instead of a plan buffer, so the plan's grid_n must be <= 512
+ * (PISCO_EINVAL otherwise).  The first call on a device looks the array's
+ * address up (once per device; make it before any stream capture).  Every
+ * call uses the same array and clears it first: calls whose kernels overlap
+ * on the GPU race.  No cudaMalloc, cudaFree or allocating library call.
+ */
+pisco_status pisco_beam_grid_adjoint_static(pisco_plan* plan, int det, int64_t n,
+                                            const double* theta, const double* phi, const double* psi,
+                                            const void* tod, void* grad_grids, int accumulate, void* stream);
+
+/*
  * pisco_omega_adjoint -- the Omega~ term of the beam gradient.  Omega~ =
  * int B_TT dOmega (Sec. 3) scales every sample by 1/Omega~, so with the
  * forward TOD d (from pisco_convolve) and its gradient y:

@@ -34,7 +34,12 @@ void set_error(pisco_plan* plan, const char* fmt, ...) {
     } while (0)
 
 // A pointer the kernels may dereference: device or managed memory of the current device.
-static bool is_device_ptr(const void* p) {
+namespace pisco {
+bool is_device_ptr(const void* p);
+pisco_status check_pointing(pisco_plan* plan, int64_t n, const double* a, const double* b, const double* c);
+}  // namespace pisco
+
+bool pisco::is_device_ptr(const void* p) {
     if (p == nullptr) return false;
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -292,8 +297,8 @@ static LaunchParams base_params(const pisco_plan* p) {
     return L;
 }
 
-static pisco_status check_pointing(pisco_plan* plan, int64_t n, const double* a, const double* b,
-                                   const double* c) {
+pisco_status pisco::check_pointing(pisco_plan* plan, int64_t n, const double* a, const double* b,
+                            const double* c) {
     if (n < 0) {
         set_error(plan, "n = %lld is negative", (long long)n);
         return PISCO_EINVAL;
@@ -306,9 +311,15 @@ static pisco_status check_pointing(pisco_plan* plan, int64_t n, const double* a,
 }
 
 // Launch one path over detectors [d0, d0 + nd) with per-detector sample ranges.
-static pisco_status run(pisco_plan* plan, int mode, int d0, int nd, const int64_t* begin, const int64_t* count,
-                        const double* theta, const double* phi, const double* psi, void* out, const void* tod_in,
-                        int32_t* counts, cudaStream_t s) {
+namespace pisco {
+pisco_status run(pisco_plan* plan, int mode, int d0, int nd, const int64_t* begin, const int64_t* count,
+                 const double* theta, const double* phi, const double* psi, void* out, const void* tod_in,
+                 int32_t* counts, cudaStream_t s);
+}  // namespace pisco
+
+pisco_status pisco::run(pisco_plan* plan, int mode, int d0, int nd, const int64_t* begin, const int64_t* count,
+                 const double* theta, const double* phi, const double* psi, void* out, const void* tod_in,
+                 int32_t* counts, cudaStream_t s) {
     const long long per_tile = plan->precision == PISCO_FP32 ? plan->tile_samples : 1;
     for (int c = 0; c < nd; c += kMaxDetPerLaunch) {
         LaunchParams L = base_params(plan);

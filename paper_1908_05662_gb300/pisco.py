@@ -26,7 +26,7 @@ STATUS_NAMES = {0: "PISCO_OK", 1: "PISCO_EINVAL", 2: "PISCO_ENOMEM", 3: "PISCO_E
 EXPORTS = ("pisco_plan_create", "pisco_plan_destroy", "pisco_last_error", "pisco_plan_omega",
            "pisco_convolve", "pisco_convolve_batched", "pisco_adjoint", "pisco_disc_count",
            "pisco_convolve_host", "pisco_sync_status", "pisco_beam_grid_adjoint", "pisco_omega_adjoint",
-           "pisco_update_beams")
+           "pisco_update_beams", "pisco_beam_grid_adjoint_static")
 
 
 class PiscoError(RuntimeError):
@@ -72,6 +72,7 @@ def load_library(path=LIB_PATH):
         "pisco_beam_grid_adjoint": (c_int, [vp, c_int, i64, vp, vp, vp, vp, vp, c_int, vp]),
         "pisco_omega_adjoint": (c_int, [vp, c_int, i64, vp, vp, vp, vp]),
         "pisco_update_beams": (c_int, [vp, vp, ctypes.POINTER(dbl), vp]),
+        "pisco_beam_grid_adjoint_static": (c_int, [vp, c_int, i64, vp, vp, vp, vp, vp, c_int, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -186,6 +187,15 @@ def pisco_beam_grid_adjoint(plan, det, theta, phi, psi, tod, grad_grids, accumul
     _check(load_library().pisco_beam_grid_adjoint(plan, det, n, _ptr(_f64(theta)), _ptr(_f64(phi)),
                                                   _ptr(_f64(psi)), _ptr(tod), _ptr(grad_grids),
                                                   int(bool(accumulate)), _stream()), plan)
+    return grad_grids
+
+
+def pisco_beam_grid_adjoint_static(plan, det, theta, phi, psi, tod, grad_grids, accumulate=False):
+    """pisco_beam_grid_adjoint without allocation (scratch in the library's static array, grid_n <= 512)."""
+    n = theta.numel()
+    _check(load_library().pisco_beam_grid_adjoint_static(plan, det, n, _ptr(_f64(theta)), _ptr(_f64(phi)),
+                                                         _ptr(_f64(psi)), _ptr(tod), _ptr(grad_grids),
+                                                         int(bool(accumulate)), _stream()), plan)
     return grad_grids
 
 
