@@ -64,11 +64,13 @@ typedef enum pisco_status {
  * differ at FP32 rounding level), never the arithmetic. */
 enum {
     PISCO_FP64_PLAIN = 0, /* FP64 throughout, one CTA per sample: the plain reference path */
-    PISCO_FP32 = 1        /* FP32 arithmetic, FP64 only where offsets would cancel */
+    PISCO_FP32 = 1,       /* FP32 arithmetic, FP64 only where offsets would cancel */
+    PISCO_BF16_MR = 2,    /* n_real sky realizations in BF16, FP32 weights rounded to BF16, tensor cores, FP32 accumulate */
+    PISCO_FP16_MR = 3     /* the same with FP16 realizations and weights */
 };
 
 /* Element type of caller arrays (sky_dtype). */
-enum { PISCO_DTYPE_F32 = 0, PISCO_DTYPE_F64 = 1 };
+enum { PISCO_DTYPE_F32 = 0, PISCO_DTYPE_F64 = 1, PISCO_DTYPE_BF16 = 2, PISCO_DTYPE_F16 = 3 };
 
 /* One detector (Sec. 3 eq. copol_bolo, Sec. 4.1 eq. M_pol): polarisation
  * angle zeta (radians) from theta'0, polarisation efficiency 1 - eps,
@@ -84,6 +86,7 @@ typedef struct pisco_options {
     int tile_samples;       /* FP32 path: consecutive samples sharing one disc traversal: 8, 16 or 32 (0 = 16) */
     int pixels_per_thread;  /* FP32 path: consecutive ring pixels per thread: 1 or 2 (0 = 1) */
     int beam_fetch;         /* FP32 path: PISCO_FETCH_CELLS or PISCO_FETCH_TEXTURE (0 = cells) */
+    int n_real;             /* PISCO_*_MR plans: realizations, a multiple of 32 in [32, 256] */
 } pisco_options;
 
 /* How the FP32 kernel reads the beam (pisco_options.beam_fetch): 64-byte
@@ -101,7 +104,10 @@ typedef struct pisco_plan pisco_plan;  /* opaque, owned by the library */
  *   nside        HEALPix resolution, 1 <= nside <= 8192.
  *   radius_rad   disc cut-off rho_max (Sec. 5.3, Table 1) = beam grid radius,
  *                0 < radius < pi/2.
- *   sky          device, [3][12 nside^2] of sky_dtype (I, Q, U; V is zero, Sec. 6.2).
+ *   sky          device, [3][12 nside^2] of sky_dtype (I, Q, U; V is zero, Sec. 6.2);
+ *                for PISCO_BF16_MR / PISCO_FP16_MR plans a realization stack
+ *                [12 nside^2][3][n_real] of PISCO_DTYPE_BF16 / PISCO_DTYPE_F16
+ *                (realizations contiguous per pixel and Stokes parameter).
  *   n_det, dets  host array of n_det >= 1 detectors.
  *   grid_n       nodes per grid side, 2 <= grid_n <= 4096.
  *   beam_grids   device float32 [n_det][6][grid_n][grid_n].
@@ -134,7 +140,12 @@ pisco_status pisco_plan_omega(const pisco_plan* plan, int det, double* omega_til
  * discrete_beam_conv_tensor; Sec. 5.2's per-pointing loop L1 over the disc loop L2).
  *   theta, phi, psi  device float64 [n].
  *   tod              device [n]: float32 for a PISCO_FP32 plan, float64 for
- *                    PISCO_FP64_PLAIN; overwritten.
+ *                    PISCO_FP64_PLAIN; float32 [n][n_real] for PISCO_*_MR plans
+ *                    (one TOD per realization, the dense contraction
+ *                    d_r(t) = sum_k W_t(k) . S_r(k) run on the tensor cores);
+ *                    overwritten.  Multi-realization plans support
+ *                    pisco_convolve and pisco_convolve_batched only
+ *                    (PISCO_EUNSUPPORTED otherwise).
  * n = 0 is a valid no-op.  Long scans may be split into consecutive calls on
  * sub-ranges (pointer offsets); results do not depend on the split.
  */

@@ -137,8 +137,20 @@ extern "C" pisco_status pisco_plan_create(pisco_plan** out, int nside, double ra
         set_error(nullptr, "radius %g outside (0, pi/2)", radius_rad);
         return PISCO_EINVAL;
     }
-    if (sky_dtype != PISCO_DTYPE_F32 && sky_dtype != PISCO_DTYPE_F64) {
+    const int precision0 = opt ? opt->precision : PISCO_FP32;
+    const bool mr = precision0 == PISCO_BF16_MR || precision0 == PISCO_FP16_MR;
+    if (!mr && sky_dtype != PISCO_DTYPE_F32 && sky_dtype != PISCO_DTYPE_F64) {
         set_error(nullptr, "sky_dtype %d is neither PISCO_DTYPE_F32 nor PISCO_DTYPE_F64", sky_dtype);
+        return PISCO_EINVAL;
+    }
+    if (mr && sky_dtype != (precision0 == PISCO_BF16_MR ? PISCO_DTYPE_BF16 : PISCO_DTYPE_F16)) {
+        set_error(nullptr, "a %s plan takes a %s realization stack", precision0 == PISCO_BF16_MR ? "BF16" : "FP16",
+                  precision0 == PISCO_BF16_MR ? "PISCO_DTYPE_BF16" : "PISCO_DTYPE_F16");
+        return PISCO_EINVAL;
+    }
+    const int n_real = mr ? opt->n_real : 1;
+    if (mr && !(n_real >= 32 && n_real <= 256 && n_real % 32 == 0)) {
+        set_error(nullptr, "n_real %d is not a multiple of 32 in [32, 256]", n_real);
         return PISCO_EINVAL;
     }
     if (n_det < 1 || !dets) {
@@ -159,9 +171,9 @@ extern "C" pisco_status pisco_plan_create(pisco_plan** out, int nside, double ra
         set_error(nullptr, "grid_n %d outside [2, 4096]", grid_n);
         return PISCO_EINVAL;
     }
-    const int precision = opt ? opt->precision : PISCO_FP32;
-    if (precision != PISCO_FP32 && precision != PISCO_FP64_PLAIN) {
-        set_error(nullptr, "precision %d is not PISCO_FP32 or PISCO_FP64_PLAIN", precision);
+    const int precision = precision0;
+    if (precision != PISCO_FP32 && precision != PISCO_FP64_PLAIN && !mr) {
+        set_error(nullptr, "precision %d is not a PISCO_* precision", precision);
         return PISCO_EINVAL;
     }
     int tile = opt && opt->tile_samples ? opt->tile_samples : 16;
@@ -175,6 +187,7 @@ extern "C" pisco_status pisco_plan_create(pisco_plan** out, int nside, double ra
         return PISCO_EINVAL;
     }
     int fetch = opt && opt->beam_fetch ? opt->beam_fetch : PISCO_FETCH_CELLS;
+    if (mr) fetch = PISCO_FETCH_CELLS;  // the multi-realization kernel reads coefficient cells
     if (fetch != PISCO_FETCH_TEXTURE && fetch != PISCO_FETCH_CELLS) {
         set_error(nullptr, "beam_fetch %d is not PISCO_FETCH_TEXTURE or PISCO_FETCH_CELLS", fetch);
         return PISCO_EINVAL;
@@ -198,6 +211,7 @@ extern "C" pisco_status pisco_plan_create(pisco_plan** out, int nside, double ra
     p->tile_samples = tile;
     p->pixels_per_thread = np;
     p->beam_fetch = fetch;
+    p->n_real = n_real;
     p->radius = radius_rad;
     p->cos_r = cos(radius_rad);
     p->omega_pix = 4.0 * kPi / (double)p->npix;
@@ -214,9 +228,11 @@ extern "C" pisco_status pisco_plan_create(pisco_plan** out, int nside, double ra
     const size_t nn = (size_t)grid_n * grid_n;
     const size_t nc = (size_t)(grid_n - 1) * (grid_n - 1);
     if (precision == PISCO_FP64_PLAIN) p->beam_stride = 3 * nn * sizeof(double);
+    else if (mr) p->beam_stride = nc * 4 * sizeof(float4);
     else if (fetch == PISCO_FETCH_CELLS) p->beam_stride = nc * 4 * sizeof(float4);
     else p->beam_stride = 0;
-    const size_t sky_bytes = precision == PISCO_FP32 ? p->npix * sizeof(float4) : 3 * p->npix * sizeof(double);
+    const size_t sky_bytes = mr ? (size_t)p->npix * 3 * n_real * 2
+                             : precision == PISCO_FP32 ? p->npix * sizeof(float4) : 3 * p->npix * sizeof(double);
     double* d_omega = nullptr;
     cudaError_t e = cudaMalloc(&p->d_rings, p->nrings * sizeof(RingInfo));
     if (e == cudaSuccess) e = cudaMalloc(&p->d_sky, sky_bytes);
@@ -232,7 +248,13 @@ extern "C" pisco_status pisco_plan_create(pisco_plan** out, int nside, double ra
     }
     cudaStream_t s = (cudaStream_t)stream;
     e = cudaMemsetAsync(p->d_err, 0, sizeof(int), s);
-    if (e == cudaSuccess) e = launch_plan_kernels(p, sky, sky_dtype, beam_grids, s, d_omega);
+    if (e == cudaSuccess && mr) {
+        // realization stacks are stored as given ([Npix][3][n_real], 16-bit)
+        e = cudaMemcpyAsync(p->d_sky, sky, sky_bytes, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) e = launch_plan_kernels(p, nullptr, -1, beam_grids, s, d_omega);
+    } else if (e == cudaSuccess) {
+        e = launch_plan_kernels(p, sky, sky_dtype, beam_grids, s, d_omega);
+    }
     if (e == cudaSuccess && precision == PISCO_FP32 && fetch == PISCO_FETCH_TEXTURE) e = build_textures(p, beam_grids, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(p->h_omega, d_omega, n_det * sizeof(double), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -320,7 +342,8 @@ pisco_status run(pisco_plan* plan, int mode, int d0, int nd, const int64_t* begi
 pisco_status pisco::run(pisco_plan* plan, int mode, int d0, int nd, const int64_t* begin, const int64_t* count,
                  const double* theta, const double* phi, const double* psi, void* out, const void* tod_in,
                  int32_t* counts, cudaStream_t s) {
-    const long long per_tile = plan->precision == PISCO_FP32 ? plan->tile_samples : 1;
+    const long long per_tile = plan->precision == PISCO_FP64_PLAIN ? 1
+                               : (plan->precision == PISCO_FP32 ? plan->tile_samples : 16);
     for (int c = 0; c < nd; c += kMaxDetPerLaunch) {
         LaunchParams L = base_params(plan);
         L.theta = theta;
@@ -347,8 +370,15 @@ pisco_status pisco::run(pisco_plan* plan, int mode, int d0, int nd, const int64_
         if (k == 0) continue;
         L.ndet = k;
         L.total_tiles = tiles;
+        L.n_real = plan->n_real;
         cudaError_t e;
-        if (plan->precision == PISCO_FP64_PLAIN) e = launch_plain(L, mode, s);
+        if (plan->precision == PISCO_BF16_MR || plan->precision == PISCO_FP16_MR) {
+            if (mode != kForward) {
+                set_error(plan, "multi-realization plans support pisco_convolve and pisco_convolve_batched only");
+                return PISCO_EUNSUPPORTED;
+            }
+            e = launch_mr(L, plan->precision == PISCO_FP16_MR, s);
+        } else if (plan->precision == PISCO_FP64_PLAIN) e = launch_plain(L, mode, s);
         else if (plan->beam_fetch == PISCO_FETCH_CELLS)
             e = launch_fast_cells(L, mode, plan->tile_samples, plan->pixels_per_thread, s);
         else e = launch_fast_texture(L, mode, plan->tile_samples, plan->pixels_per_thread, s);
@@ -462,6 +492,10 @@ extern "C" pisco_status pisco_convolve_host(pisco_plan* plan, int det, int64_t n
     if (n < 0 || (n > 0 && (!h_theta || !h_phi || !h_psi || !h_tod))) {
         set_error(plan, "bad host buffers or n");
         return PISCO_EINVAL;
+    }
+    if (plan->n_real > 1) {
+        set_error(plan, "pisco_convolve_host does not take multi-realization plans");
+        return PISCO_EUNSUPPORTED;
     }
     if (n == 0) return PISCO_OK;
     const size_t out_elem = plan->precision == PISCO_FP32 ? sizeof(float) : sizeof(double);

@@ -62,6 +62,7 @@ struct LaunchParams {
     const void* tod_in;    // adjoint input
     int32_t* counts;       // count mode output
     int* err;
+    int n_real;            // multi-realization plans: realizations per pixel
     int ndet;
     long long total_tiles;
     DetEntry det[kMaxDetPerLaunch];
@@ -79,6 +80,7 @@ struct pisco_plan {
     int tile_samples;
     int pixels_per_thread;
     int beam_fetch;    // PISCO_FETCH_CELLS or PISCO_FETCH_TEXTURE
+    int n_real;        // realizations (multi-realization plans), else 1
     double radius;
     double cos_r;
     double omega_pix;
@@ -107,6 +109,7 @@ namespace pisco {
 cudaError_t launch_fast_texture(const LaunchParams& p, int mode, int tile_samples, int np, cudaStream_t s);
 cudaError_t launch_fast_cells(const LaunchParams& p, int mode, int tile_samples, int np, cudaStream_t s);
 cudaError_t launch_plain(const LaunchParams& p, int mode, cudaStream_t s);
+cudaError_t launch_mr(const LaunchParams& p, int f16, cudaStream_t s);
 cudaError_t launch_plan_kernels(pisco_plan* plan, const void* sky, int sky_dtype,
                                 const float* grids, cudaStream_t s, double* d_omega_out);
 cudaError_t launch_fold_nodes32(const float* grids, int n, double eps, double zeta, float* out3, cudaStream_t s);

@@ -251,7 +251,7 @@ cudaError_t launch_beam_kernels(pisco_plan* plan, const float* grids, cudaStream
         const float* g = grids + (long long)d * 6 * nn;
         char* dst = plan->d_beam ? (char*)plan->d_beam + (size_t)d * plan->beam_stride : nullptr;
         const pisco_detector& det = plan->h_dets[d];
-        if (plan->precision == PISCO_FP32) {
+        if (plan->precision != PISCO_FP64_PLAIN) {
             if (plan->beam_fetch == PISCO_FETCH_CELLS) {
                 const long long nc = (long long)(n - 1) * (n - 1);
                 k_cells<<<blocks_for(nc, 256), 256, 0, s>>>(g, n, det.eps, det.zeta, (float4*)dst);
@@ -268,7 +268,9 @@ cudaError_t launch_plan_kernels(pisco_plan* plan, const void* sky, int sky_dtype
                                 cudaStream_t s, double* d_omega_out) {
     k_rings<<<blocks_for(plan->nrings, 128), 128, 0, s>>>(plan->nside, plan->nrings, plan->d_rings);
     const long long npix = plan->npix;
-    if (plan->precision == PISCO_FP32) {
+    if (sky_dtype < 0) {
+        // sky already in place (multi-realization plans)
+    } else if (plan->precision == PISCO_FP32) {
         if (sky_dtype == PISCO_DTYPE_F32)
             k_sky32<float><<<blocks_for(npix, 256), 256, 0, s>>>((const float*)sky, npix, (float4*)plan->d_sky);
         else

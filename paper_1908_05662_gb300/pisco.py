@@ -15,8 +15,8 @@ import torch
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libpisco.so")
 
 PISCO_OK, PISCO_EINVAL, PISCO_ENOMEM, PISCO_ECUDA, PISCO_ETIMEOUT, PISCO_EUNSUPPORTED, PISCO_EDEVICE = range(7)
-PISCO_FP64_PLAIN, PISCO_FP32 = 0, 1
-PISCO_DTYPE_F32, PISCO_DTYPE_F64 = 0, 1
+PISCO_FP64_PLAIN, PISCO_FP32, PISCO_BF16_MR, PISCO_FP16_MR = 0, 1, 2, 3
+PISCO_DTYPE_F32, PISCO_DTYPE_F64, PISCO_DTYPE_BF16, PISCO_DTYPE_F16 = 0, 1, 2, 3
 PISCO_FETCH_TEXTURE, PISCO_FETCH_CELLS = 1, 2
 
 STATUS_NAMES = {0: "PISCO_OK", 1: "PISCO_EINVAL", 2: "PISCO_ENOMEM", 3: "PISCO_ECUDA",
@@ -41,7 +41,7 @@ class pisco_detector(ctypes.Structure):
 
 class pisco_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("tile_samples", ctypes.c_int),
-                ("pixels_per_thread", ctypes.c_int), ("beam_fetch", ctypes.c_int)]
+                ("pixels_per_thread", ctypes.c_int), ("beam_fetch", ctypes.c_int), ("n_real", ctypes.c_int)]
 
 
 _lib = None
@@ -108,7 +108,12 @@ def pisco_plan_create(nside, radius, sky, dets, beam_grids, omega_tilde=None,
     (float32 or float64); dets: list of (zeta, eps, s_resp); beam_grids: (n_det, 6, N, N)
     float32 CUDA tensor."""
     lib = load_library()
-    if sky.dtype not in (torch.float32, torch.float64) or not sky.is_cuda:
+    mr = precision in (PISCO_BF16_MR, PISCO_FP16_MR)
+    if mr:
+        want = torch.bfloat16 if precision == PISCO_BF16_MR else torch.float16
+        if sky.dtype != want or not sky.is_cuda or sky.dim() != 3 or sky.shape[1] != 3:
+            raise ValueError(f"a multi-realization plan takes a ({12 * nside * nside}, 3, n_real) {want} CUDA tensor")
+    elif sky.dtype not in (torch.float32, torch.float64) or not sky.is_cuda:
         raise ValueError("sky must be a float32/float64 CUDA tensor")
     if beam_grids.dtype != torch.float32 or not beam_grids.is_cuda:
         raise ValueError("beam_grids must be a float32 CUDA tensor")
@@ -117,14 +122,18 @@ def pisco_plan_create(nside, radius, sky, dets, beam_grids, omega_tilde=None,
     if beam_grids.dim() != 4 or beam_grids.shape[0] != n_det or beam_grids.shape[1] != 6 \
             or beam_grids.shape[2] != beam_grids.shape[3]:
         raise ValueError("beam_grids must have shape (n_det, 6, N, N)")
-    if tuple(sky.shape) != (3, 12 * nside * nside):
+    if not mr and tuple(sky.shape) != (3, 12 * nside * nside):
         raise ValueError("sky must have shape (3, 12 nside^2)")
+    if mr and sky.shape[0] != 12 * nside * nside:
+        raise ValueError("the realization stack must have shape (12 nside^2, 3, n_real)")
     arr = (pisco_detector * n_det)(*[pisco_detector(*map(float, d)) for d in dets])
     om = None if omega_tilde is None else (ctypes.c_double * n_det)(*map(float, omega_tilde))
-    opt = pisco_options(precision, tile_samples, pixels_per_thread, beam_fetch)
+    n_real = int(sky.shape[2]) if mr else 1
+    opt = pisco_options(precision, tile_samples, pixels_per_thread, beam_fetch, n_real)
     handle = ctypes.c_void_p()
-    st = lib.pisco_plan_create(ctypes.byref(handle), int(nside), float(radius), _ptr(sky),
-                               PISCO_DTYPE_F64 if sky.dtype == torch.float64 else PISCO_DTYPE_F32,
+    dtype_code = {torch.float64: PISCO_DTYPE_F64, torch.float32: PISCO_DTYPE_F32,
+                  torch.bfloat16: PISCO_DTYPE_BF16, torch.float16: PISCO_DTYPE_F16}[sky.dtype]
+    st = lib.pisco_plan_create(ctypes.byref(handle), int(nside), float(radius), _ptr(sky), dtype_code,
                                n_det, arr, int(beam_grids.shape[-1]), _ptr(beam_grids), om,
                                ctypes.byref(opt), _stream())
     _check(st)
@@ -225,22 +234,28 @@ class Plan:
         self.nside, self.radius, self.precision = nside, radius, precision
         self.n_det = len(dets)
         self.grid_n = int(beam_grids.shape[-1])
+        self.n_real = int(sky.shape[2]) if precision in (PISCO_BF16_MR, PISCO_FP16_MR) else 1
         self.handle = pisco_plan_create(nside, radius, sky, dets, beam_grids, omega_tilde, precision,
                                         tile_samples, pixels_per_thread, beam_fetch)
 
     @property
     def out_dtype(self):
-        return torch.float32 if self.precision == PISCO_FP32 else torch.float64
+        return torch.float64 if self.precision == PISCO_FP64_PLAIN else torch.float32
+
+    def _out_shape(self, n):
+        return (n, self.n_real) if self.n_real > 1 else (n,)
 
     def omega(self, det=0):
         return pisco_plan_omega(self.handle, det)
 
     def convolve(self, theta, phi, psi, det=0, out=None):
-        out = torch.empty(theta.numel(), dtype=self.out_dtype, device=theta.device) if out is None else out
+        if out is None:
+            out = torch.empty(self._out_shape(theta.numel()), dtype=self.out_dtype, device=theta.device)
         return pisco_convolve(self.handle, det, theta, phi, psi, out)
 
     def convolve_batched(self, offsets, theta, phi, psi, out=None):
-        out = torch.empty(theta.numel(), dtype=self.out_dtype, device=theta.device) if out is None else out
+        if out is None:
+            out = torch.empty(self._out_shape(theta.numel()), dtype=self.out_dtype, device=theta.device)
         return pisco_convolve_batched(self.handle, offsets, theta, phi, psi, out)
 
     def adjoint(self, theta, phi, psi, tod, det=0, maps=None, accumulate=False):
