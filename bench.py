@@ -62,6 +62,9 @@ def parse():
     ap.add_argument("--impl", default="pisco", choices=["pisco", "reference"])
     ap.add_argument("--samples", type=int, default=WORKLOAD["n_samples"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline leg")
+    ap.add_argument("--workload", default="single", choices=["single", "focalplane", "multireal", "table1"],
+                    help="single: the default single-detector line; the others measure the focal-plane, "
+                         "multi-realization and Table 1 replica configurations")
     return ap.parse_args()
 
 
@@ -213,11 +216,195 @@ def run_reference(args, rank, world):
     }))
 
 
+def _event_time(fn, steps, warmup, stream):
+    """Mean device time (ms) of fn() over ``steps`` runs after ``warmup`` runs, CUDA events on ``stream``."""
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def run_focalplane(args, dev):
+    """64 detectors, focal-plane offsets within +-10 deg, FWHM 1.2-1.8 deg, ellipticity 0-0.1, own
+    201^2 grids of radius 6 deg, scan lengths uniform in [1e5, 5e6], nside 256 sky: one batched
+    launch per step, replayed from a captured CUDA graph."""
+    nside, r, n_det = 256, math.radians(6.0), 64
+    rng = np.random.default_rng(3)
+    lengths = rng.integers(100_000, 5_000_001, n_det)
+    if args.samples != WORKLOAD["n_samples"]:
+        lengths = np.maximum(1, (lengths * (args.samples / lengths.sum())).astype(np.int64))
+    off, fwhm, ell, zeta = sy.focal_plane(n_det, 3)
+    sky = cached_sky(nside, 1, dev)
+    grids = np.stack([sy.gaussian_beam_maps(201, r, fwhm[d], ellipticity=ell[d]) for d in range(n_det)])
+    dets = [(float(zeta[d]), 0.0, 1.0) for d in range(n_det)]
+    parts = [sy.ces_scan(int(lengths[d]), offset=tuple(off[d]), device=dev) for d in range(n_det)]
+    th, ph, ps = (torch.cat([p[k] for p in parts]).contiguous() for k in range(3))
+    del parts
+    offsets = [0] + list(np.cumsum(lengths))
+    n = int(offsets[-1])
+    plan = pisco.Plan(nside, r, sky, dets, torch.as_tensor(grids, device=dev).contiguous())
+    pairs = int(plan.disc_count(th, ph).to(torch.int64).sum().item())
+    tod = torch.empty(n, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    plan.convolve_batched(offsets, th, ph, ps, out=tod)
+    torch.cuda.synchronize()
+    graph = None
+    try:
+        s = torch.cuda.Stream()
+        s.wait_stream(stream)
+        with torch.cuda.stream(s):
+            plan.convolve_batched(offsets, th, ph, ps, out=tod)
+        stream.wait_stream(s)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            plan.convolve_batched(offsets, th, ph, ps, out=tod)
+        step = graph.replay
+    except Exception as e:  # capture unavailable: time the eager launch instead
+        graph_error = str(e)
+        step = lambda: plan.convolve_batched(offsets, th, ph, ps, out=tod)
+    with ClockSampler(torch.cuda.current_device()) as clocks:
+        ms = _event_time(step, args.steps, args.warmup, stream)
+    plan.sync_status()
+    achieved = FLOPS_PER_PAIR * pairs / (ms / 1e3) / 1e12
+    out = {"metric": "TOD samples/s (64-detector focal plane, nside 256, R 6 deg, 201^2 grids)",
+           "value": n / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic",
+           "config": {"workload": "focal plane: 64 detectors, offsets +-10 deg, FWHM 1.2-1.8 deg, e 0-0.1, "
+                                  "201^2 grids of radius 6 deg, scan lengths U[1e5, 5e6], nside 256",
+                      "samples": n, "pairs_per_step": pairs, "launch": "cuda graph" if graph else "eager",
+                      "l2": "inputs larger than L2"},
+           "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                        "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None},
+           "gpu_launches": args.steps, "clocks": clocks.summary()}
+    if graph is None:
+        out["graph_error"] = graph_error
+    plan.close()
+    print(json.dumps(out))
+
+
+def run_multireal(args, dev):
+    """256 realizations at nside 256 stored BF16 and FP16 (random combinations of 16 seeded base
+    fields, which keeps C_l), one detector, 2e6 samples of the azimuth scan, 1.5 deg Gaussian beam
+    of radius 4 deg on a 161^2 grid."""
+    nside, r, n_real = 256, math.radians(4.0), 256
+    n = 2_000_000 if args.samples == WORKLOAD["n_samples"] else args.samples
+    gen = torch.Generator().manual_seed(1000)
+    coef = (torch.randn(n_real, 16, generator=gen, dtype=torch.float64) / 4.0).to(dev)
+    base = torch.stack([cached_sky(nside, 1000 + k, dev) for k in range(16)])
+    exact = torch.einsum("rk,kmp->pmr", coef, base).contiguous()
+    del base
+    grids = sy.gaussian_beam_maps(161, r, 1.5)
+    g = torch.as_tensor(grids, device=dev)[None]
+    th, ph, ps = (x.contiguous() for x in sy.ces_scan(n, device=dev))
+    det = (0.0, 0.0, 1.0)
+    stream = torch.cuda.current_stream()
+    results = {}
+    for name, precision, dtype in (("bf16", pisco.PISCO_BF16_MR, torch.bfloat16),
+                                   ("fp16", pisco.PISCO_FP16_MR, torch.float16)):
+        plan = pisco.Plan(nside, r, exact.to(dtype), [det], g, precision=precision)
+        out = torch.empty(n, n_real, dtype=torch.float32, device=dev)
+        with ClockSampler(torch.cuda.current_device()) as clocks:
+            ms = _event_time(lambda: plan.convolve(th, ph, ps, out=out), args.steps, args.warmup, stream)
+        plan.sync_status()
+        results[name] = (ms, clocks.summary(), out[::20000].double().cpu().numpy())
+        plan.close()
+    pairs = int(pisco.Plan(nside, r, exact[:, :, 0].T.contiguous(), [det], g).disc_count(th, ph)
+                .to(torch.int64).sum().item())
+    # error against the FP64 oracle on the unrounded realizations, every 20000th sample
+    from oracle import beam as ob
+    from oracle import convolve as oc
+    g64 = grids.astype(np.float64)
+    omega = ob.omega_tilde(g64[0], r)
+    idx = np.arange(0, n, 20000)
+    thn, phn, psn = th.cpu().numpy(), ph.cpu().numpy(), ps.cpu().numpy()
+    ref = np.empty((len(idx), n_real))
+    for k, t in enumerate(idx):
+        pix, w = oc.sample_weights(nside, r, g64, det, omega, thn[t], phn[t], psn[t])
+        ref[k] = np.einsum("km,kmr->r", w, exact[torch.as_tensor(pix, device=dev)].cpu().numpy())
+    errs = {k: float(np.max(np.max(np.abs(v[2] - ref), axis=0) / np.max(np.abs(ref), axis=0)))
+            for k, v in results.items()}
+    ms, clk, _ = results["bf16"]
+    algo = 2.0 * 3 * pairs * n_real  # one FMA per (pair, Stokes, realization)
+    achieved = algo / (ms / 1e3) / 1e12
+    print(json.dumps({
+        "metric": "TOD samples/s (256 realizations per sample, BF16 stack, nside 256, R 4 deg)",
+        "value": n / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+        "data": "synthetic",
+        "config": {"workload": "multi-realization: 256 realizations at nside 256 (BF16; combinations of 16 "
+                               "base fields), 2e6 scan samples, 1.5 deg beam of radius 4 deg, 161^2 grid",
+                   "samples": n, "realizations": n_real, "pairs_per_step": pairs},
+        "realization_samples_per_s": n * n_real / (ms / 1e3),
+        "fp16": {"ms_per_step": results["fp16"][0], "value": n / (results["fp16"][0] / 1e3)},
+        "err_vs_oracle_normwise_per_realization": errs,
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": 1927.2, "unit": "TFLOP/s",
+                     "frac": achieved / 1927.2, "traffic": None,
+                     "note": "algorithmic 2*3*pairs*R flops (the hi/lo weight split doubles the issued MMAs); "
+                             "bf16 peak of measured"},
+        "gpu_launches": args.steps, "clocks": clk}))
+
+
+def run_table1(args, dev):
+    """The paper's Table 1 setup (Sec. 5.3.1): 2 detectors (zeta 0 and -90 deg) x 3 position angles
+    (0, 45, 90 deg) x every nside-128 pixel centre = 1,179,648 samples, Gaussian FWHM 1.5 deg,
+    rho_max 5-30 deg; wall time includes building the beam grid and plan, the host<->GPU copies and
+    the convolution, as in the paper.  Beam grid spacing 0.1145 deg (the pixel size of the paper's
+    nside-512 beam)."""
+    nside = 128
+    th_c, ph_c = sy.healpix_centres(nside)
+    angles = np.radians([0.0, 45.0, 90.0])
+    th = np.repeat(th_c, 3)
+    ph = np.repeat(ph_c, 3)
+    ps = np.tile(angles, len(th_c))
+    h = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (th, ph, ps)]
+    sky_h = cached_sky(nside, 1, "cuda").cpu().pin_memory()
+    paper = {5.0: 1471.41, 7.5: 3135.19, 10.0: 5560.25, 15.0: 12719.56, 20.0: 23190.68, 25.0: 39447.70,
+             30.0: 53800.74}
+    rows = []
+    for rho, paper_ms in paper.items():
+        r = math.radians(rho)
+        n_grid = int(round(2 * math.sin(r) / math.radians(0.1145))) + 1
+        best = None
+        for rep in range(2):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            grids_h = torch.from_numpy(np.stack([sy.gaussian_beam_maps(n_grid, r, 1.5, ideal=True)] * 2))
+            sky = sky_h.to(dev, non_blocking=True)
+            g = grids_h.to(dev)
+            plan = pisco.Plan(nside, r, sky, [(0.0, 0.0, 1.0), (-math.pi / 2, 0.0, 1.0)], g)
+            outs = [torch.empty(len(th), dtype=torch.float32).pin_memory() for _ in range(2)]
+            for d in range(2):
+                plan.convolve_host(*h, det=d, out=outs[d])
+            wall = time.perf_counter() - t0
+            plan.close()
+            best = wall if best is None else min(best, wall)
+        rows.append({"rho_max_deg": rho, "grid_n": n_grid, "wall_ms": 1e3 * best, "paper_ms_gtx1080": paper_ms,
+                     "samples_per_s": 2 * len(th) / best, "speedup_vs_paper": paper_ms / (1e3 * best)})
+    print(json.dumps({"metric": "Table 1 replica: wall time of a whole-sky PSB convolution", "unit": "ms",
+                      "higher_is_better": False, "dtype": "f32", "data": "synthetic",
+                      "config": {"workload": "2 detectors x 3 angles x nside-128 pixel centres = 1,179,648 "
+                                             "samples, FWHM 1.5 deg, rho_max 5-30 deg, copies included"},
+                      "rows": rows}))
+
+
 def main():
     args = parse()
     rank, world, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload != "single":
+        torch.cuda.set_device(local)
+        {"focalplane": run_focalplane, "multireal": run_multireal, "table1": run_table1}[args.workload](
+            args, torch.device("cuda", local))
         return
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)

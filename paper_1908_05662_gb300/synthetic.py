@@ -229,6 +229,15 @@ def ces_scan(n, rate_hz=20.0, latitude_deg=-23.0, elevation_deg=45.0, az_speed_d
     return theta, ra, psi
 
 
+def healpix_centres(nside):
+    """(theta, phi) float64 of every RING pixel centre (pointings on pixel centres)."""
+    th, ph = [], []
+    for z, phi0, cnt in _ring_layout(nside):
+        th.append(np.full(cnt, math.atan2(math.sqrt((1.0 - z) * (1.0 + z)), z)))
+        ph.append(phi0 + np.arange(cnt) * (2.0 * math.pi / cnt))
+    return np.concatenate(th), np.concatenate(ph)
+
+
 def focal_plane(n_det, seed, max_offset_deg=10.0):
     """Seeded focal-plane offsets (radians) and beam parameters for ``n_det`` detectors."""
     rng = np.random.default_rng(seed)
