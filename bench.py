@@ -62,9 +62,10 @@ def parse():
     ap.add_argument("--impl", default="pisco", choices=["pisco", "reference"])
     ap.add_argument("--samples", type=int, default=WORKLOAD["n_samples"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline leg")
-    ap.add_argument("--workload", default="single", choices=["single", "focalplane", "multireal", "table1"],
+    ap.add_argument("--workload", default="single",
+                    choices=["single", "focalplane", "multireal", "table1", "psb"],
                     help="single: the default single-detector line; the others measure the focal-plane, "
-                         "multi-realization and Table 1 replica configurations")
+                         "multi-realization, Table 1 replica and PSB-pair (shared geometry) configurations")
     return ap.parse_args()
 
 
@@ -352,6 +353,50 @@ def run_multireal(args, dev):
         "gpu_launches": args.steps, "clocks": clk}))
 
 
+def run_psb(args, dev):
+    """A PSB pair (zeta 0 and -90 deg, matched beams) on the default single-detector workload: one
+    pisco_convolve_psb pass per step writes both TODs; two pisco_convolve calls are timed beside it."""
+    from oracle import beam as ob
+    from oracle import convolve as oc
+    n = args.samples
+    r, sky, grids, (th, ph, ps) = make_workload(dev, n)
+    g = torch.as_tensor(grids, device=dev)[None].contiguous()
+    zetas = [0.0, -math.pi / 2]
+    plan = pisco.Plan(WORKLOAD["nside"], r, sky, [(0.0, 0.0, 1.0)], g, tile_samples=WORKLOAD["tile_samples"])
+    pairs = int(plan.disc_count(th, ph).to(torch.int64).sum().item())
+    tod2 = torch.empty(2, n, dtype=torch.float32, device=dev)
+    tod = torch.empty(n, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    with ClockSampler(torch.cuda.current_device()) as clocks:
+        ms = _event_time(lambda: plan.convolve_psb(th, ph, ps, zetas, out=tod2), args.steps, args.warmup, stream)
+    ms_fwd = _event_time(lambda: plan.convolve(th, ph, ps, out=tod), args.steps, args.warmup, stream)
+    plan.sync_status()
+    # both rows against the FP64 oracle for a detector at each angle, first 24 samples
+    k = 24
+    skyn, g64 = sky.cpu().numpy(), np.asarray(grids, np.float64)
+    omega = ob.omega_tilde(g64[0], r)
+    thn, phn, psn = (a[:k].cpu().numpy() for a in (th, ph, ps))
+    err = 0.0
+    for row, z in enumerate(zetas):
+        ref = oc.tod(WORKLOAD["nside"], r, skyn, g64, (z, 0.0, 1.0), omega, thn, phn, psn)
+        err = max(err, float(np.max(np.abs(tod2[row, :k].double().cpu().numpy() - ref)) / np.max(np.abs(ref))))
+    achieved = FLOPS_PER_PAIR * pairs / (ms / 1e3) / 1e12
+    out = {"metric": "TOD samples/s of a PSB pair (2 TODs per pointing, nside 512, R 10 deg, 501^2 grid)",
+           "value": 2 * n / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic",
+           "config": {"workload": "PSB pair (zeta 0, -90 deg) on the single-detector workload: " + WORKLOAD["workload"],
+                      "samples": n, "pairs_per_step": pairs, "l2": "inputs larger than L2"},
+           "two_forward_calls_ms": 2 * ms_fwd, "pass_over_one_forward": ms / ms_fwd,
+           "err_vs_oracle_normwise_first_24": err,
+           "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                        "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                        "note": "forward flops per pair (the pass adds 4 FMAs per pair)"},
+           "gpu_launches": args.steps, "clocks": clocks.summary()}
+    plan.close()
+    print(json.dumps(out))
+
+
 def run_table1(args, dev):
     """The paper's Table 1 setup (Sec. 5.3.1): 2 detectors (zeta 0 and -90 deg) x 3 position angles
     (0, 45, 90 deg) x every nside-128 pixel centre = 1,179,648 samples, Gaussian FWHM 1.5 deg,
@@ -386,8 +431,25 @@ def run_table1(args, dev):
             wall = time.perf_counter() - t0
             plan.close()
             best = wall if best is None else min(best, wall)
+        # the same two TODs from one shared-geometry pass (pisco_convolve_psb), copies included
+        best_psb = None
+        for rep in range(2):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            grids_h = torch.from_numpy(sy.gaussian_beam_maps(n_grid, r, 1.5, ideal=True)[None])
+            sky = sky_h.to(dev, non_blocking=True)
+            g = grids_h.to(dev)
+            plan = pisco.Plan(nside, r, sky, [(0.0, 0.0, 1.0)], g)
+            d = [a.to(dev, non_blocking=True) for a in h]
+            out = torch.empty(2, len(th), dtype=torch.float32).pin_memory()
+            out.copy_(plan.convolve_psb(*d, [0.0, -math.pi / 2]), non_blocking=True)
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+            plan.close()
+            best_psb = wall if best_psb is None else min(best_psb, wall)
         rows.append({"rho_max_deg": rho, "grid_n": n_grid, "wall_ms": 1e3 * best, "paper_ms_gtx1080": paper_ms,
-                     "samples_per_s": 2 * len(th) / best, "speedup_vs_paper": paper_ms / (1e3 * best)})
+                     "samples_per_s": 2 * len(th) / best, "speedup_vs_paper": paper_ms / (1e3 * best),
+                     "wall_ms_psb_pass": 1e3 * best_psb, "speedup_psb_vs_paper": paper_ms / (1e3 * best_psb)})
     print(json.dumps({"metric": "Table 1 replica: wall time of a whole-sky PSB convolution", "unit": "ms",
                       "higher_is_better": False, "dtype": "f32", "data": "synthetic",
                       "config": {"workload": "2 detectors x 3 angles x nside-128 pixel centres = 1,179,648 "
@@ -403,7 +465,7 @@ def main():
         return
     if args.workload != "single":
         torch.cuda.set_device(local)
-        {"focalplane": run_focalplane, "multireal": run_multireal, "table1": run_table1}[args.workload](
+        {"focalplane": run_focalplane, "multireal": run_multireal, "table1": run_table1, "psb": run_psb}[args.workload](
             args, torch.device("cuda", local))
         return
     torch.cuda.set_device(local)

@@ -166,6 +166,29 @@ pisco_status pisco_convolve_batched(pisco_plan* plan, int n_det, const int64_t* 
                                     void* tod, void* stream);
 
 /*
+ * pisco_convolve_psb -- TODs of detectors that share detector `det`'s beam,
+ * pointing, eps and s and differ only in their polarisation angle, from one
+ * traversal of the discs (Sec. 3 eq. copol_bolo: a PSB is a pair at zeta and
+ * zeta - 90 deg; Sec. 5.3's benchmark convolves two such detectors with the
+ * same beams).  zeta enters d_t only as e^{2 i zeta} on the polarised part of
+ * the folded beam, so the kernel accumulates the intensity part and the
+ * complex polarised part once and writes, for every k,
+ *   tod[k][t] = pisco_convolve's d_t for a detector with zeta = zeta[k].
+ *   zeta    host [n_zeta] polarisation angles in radians (1 <= n_zeta <= 8);
+ *           they replace detector det's own zeta.
+ *   tod     device float32 [n_zeta][n] (row k = angle k); overwritten, NaN for
+ *           invalid pointings as in pisco_convolve.
+ * FP32 plans with PISCO_FETCH_CELLS only (PISCO_EUNSUPPORTED otherwise); the
+ * pass runs the FP32 kernel with three accumulators per sample, so its
+ * results agree with n_zeta pisco_convolve calls to FP32 rounding, not
+ * bit for bit.  The paper computes each detector separately; this pass is an
+ * evaluation of the same sums that shares their geometry.
+ */
+pisco_status pisco_convolve_psb(pisco_plan* plan, int det, int64_t n,
+                                const double* theta, const double* phi, const double* psi,
+                                int n_zeta, const double* zeta, void* tod, void* stream);
+
+/*
  * pisco_adjoint -- transpose of pisco_convolve with respect to the sky:
  * maps[m][k] (+)= sum_t tod[t] * d d_t / d S^m_k for m = I, Q, U.
  *   tod    device [n], float32 (FP32 plan) or float64 (plain plan).

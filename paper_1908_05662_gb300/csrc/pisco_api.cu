@@ -34,10 +34,6 @@ void set_error(pisco_plan* plan, const char* fmt, ...) {
     } while (0)
 
 // A pointer the kernels may dereference: device or managed memory of the current device.
-namespace pisco {
-bool is_device_ptr(const void* p);
-pisco_status check_pointing(pisco_plan* plan, int64_t n, const double* a, const double* b, const double* c);
-}  // namespace pisco
 
 bool pisco::is_device_ptr(const void* p) {
     if (p == nullptr) return false;
@@ -332,16 +328,9 @@ pisco_status pisco::check_pointing(pisco_plan* plan, int64_t n, const double* a,
     return PISCO_OK;
 }
 
-// Launch one path over detectors [d0, d0 + nd) with per-detector sample ranges.
-namespace pisco {
-pisco_status run(pisco_plan* plan, int mode, int d0, int nd, const int64_t* begin, const int64_t* count,
-                 const double* theta, const double* phi, const double* psi, void* out, const void* tod_in,
-                 int32_t* counts, cudaStream_t s);
-}  // namespace pisco
-
 pisco_status pisco::run(pisco_plan* plan, int mode, int d0, int nd, const int64_t* begin, const int64_t* count,
                  const double* theta, const double* phi, const double* psi, void* out, const void* tod_in,
-                 int32_t* counts, cudaStream_t s) {
+                 int32_t* counts, cudaStream_t s, const PsbAngles* psb) {
     const long long per_tile = plan->precision == PISCO_FP64_PLAIN ? 1
                                : (plan->precision == PISCO_FP32 ? plan->tile_samples : 16);
     for (int c = 0; c < nd; c += kMaxDetPerLaunch) {
@@ -371,6 +360,14 @@ pisco_status pisco::run(pisco_plan* plan, int mode, int d0, int nd, const int64_
         L.ndet = k;
         L.total_tiles = tiles;
         L.n_real = plan->n_real;
+        if (psb) {
+            L.n_zeta = psb->n;
+            L.out_stride = psb->stride;
+            for (int k = 0; k < psb->n; ++k) {
+                L.psb_c2z[k] = psb->c2z[k];
+                L.psb_s2z[k] = psb->s2z[k];
+            }
+        }
         cudaError_t e;
         if (plan->precision == PISCO_BF16_MR || plan->precision == PISCO_FP16_MR) {
             if (mode != kForward) {
@@ -442,6 +439,47 @@ extern "C" pisco_status pisco_convolve_batched(pisco_plan* plan, int n_det, cons
                  (cudaStream_t)stream);
     free(count);
     return st;
+}
+
+extern "C" pisco_status pisco_convolve_psb(pisco_plan* plan, int det, int64_t n, const double* theta,
+                                           const double* phi, const double* psi, int n_zeta, const double* zeta,
+                                           void* tod, void* stream) {
+    if (!plan) return PISCO_EINVAL;
+    if (det < 0 || det >= plan->n_det) {
+        set_error(plan, "detector %d outside [0, %d)", det, plan->n_det);
+        return PISCO_EINVAL;
+    }
+    if (n_zeta < 1 || n_zeta > kMaxPsb || !zeta) {
+        set_error(plan, "n_zeta %d outside [1, %d] or zeta NULL", n_zeta, kMaxPsb);
+        return PISCO_EINVAL;
+    }
+    for (int k = 0; k < n_zeta; ++k)
+        if (!std::isfinite(zeta[k])) {
+            set_error(plan, "zeta[%d] is not finite", k);
+            return PISCO_EINVAL;
+        }
+    if (plan->precision != PISCO_FP32 || plan->beam_fetch != PISCO_FETCH_CELLS) {
+        set_error(plan, "pisco_convolve_psb needs an FP32 plan with PISCO_FETCH_CELLS");
+        return PISCO_EUNSUPPORTED;
+    }
+    pisco_status st = check_pointing(plan, n, theta, phi, psi);
+    if (st != PISCO_OK) return st;
+    if (n == 0) return PISCO_OK;
+    if (!is_device_ptr(tod)) {
+        set_error(plan, "tod must be a device pointer");
+        return PISCO_EINVAL;
+    }
+    PsbAngles a;
+    a.n = n_zeta;
+    a.stride = n;
+    for (int k = 0; k < n_zeta; ++k) {
+        const double d = 2.0 * (zeta[k] - plan->h_dets[det].zeta);
+        a.c2z[k] = (float)cos(d);
+        a.s2z[k] = (float)sin(d);
+    }
+    const int64_t begin = 0, count = n;
+    return run(plan, kPsb, det, 1, &begin, &count, theta, phi, psi, tod, nullptr, nullptr, (cudaStream_t)stream,
+               &a);
 }
 
 extern "C" pisco_status pisco_adjoint(pisco_plan* plan, int det, int64_t n, const double* theta,

@@ -232,9 +232,15 @@ __global__ void __launch_bounds__(NT, 2) k_fast(const __grid_constant__ LaunchPa
             }
             __syncthreads();
 
-            float acc[S];
+            // forward / count: acc.  Shared-geometry pass: acc = intensity part and accR + i accM =
+            // polarised part for the cells' own zeta; another angle zeta_k multiplies the
+            // polarised part by e^{2 i (zeta_k - zeta)}: zeta enters only through the folding's
+            // e^{2 i zeta} (Sec. 3 eq. copol_bolo; a PSB pair is zeta and zeta - 90 deg)
+            float acc[S], accR[MODE == kPsb ? S : 1], accM[MODE == kPsb ? S : 1];
 #pragma unroll
             for (int i = 0; i < S; ++i) acc[i] = 0.f;
+#pragma unroll
+            for (int i = 0; i < (MODE == kPsb ? S : 1); ++i) accR[i] = accM[i] = 0.f;
 
             const int rlo = sRlo, rhi = sRhi;
             for (int c0 = rlo; c0 <= rhi; c0 += RC) {
@@ -482,6 +488,12 @@ __global__ void __launch_bounds__(NT, 2) k_fast(const __grid_constant__ LaunchPa
                                 const float al = fmaf(re, qp[p4], -2.f * im2 * up[p4]);
                                 const float be = fmaf(2.f * im2, qp[p4], re * up[p4]);
                                 acc[i] = fmaf(bA, ip[p4], fmaf(bB, al, fmaf(bC, be, acc[i])));
+                            } else if (MODE == kPsb) {
+                                const float al = fmaf(re, qp[p4], -2.f * im2 * up[p4]);
+                                const float be = fmaf(2.f * im2, qp[p4], re * up[p4]);
+                                acc[i] = fmaf(bA, ip[p4], acc[i]);
+                                accR[i] = fmaf(bB, al, fmaf(bC, be, accR[i]));
+                                accM[i] = fmaf(bC, al, fmaf(-bB, be, accM[i]));
                             } else {
                                 const float yv = sY[i];
                                 gI[p4] = fmaf(yv, bA, gI[p4]);
@@ -530,10 +542,36 @@ __global__ void __launch_bounds__(NT, 2) k_fast(const __grid_constant__ LaunchPa
                 }
                 __syncthreads();
             }
+            if (MODE == kPsb) {
+                double part[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+#pragma unroll
+                    for (int i = 0; i < S; ++i) {
+                        if (i < gs || i >= ge) continue;
+                        float v = c == 0 ? acc[i] : (c == 1 ? accR[i] : accM[i]);
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                        if (lane == 0) sRed[warp][i] = v;
+                    }
+                    __syncthreads();
+                    if (tid >= gs && tid < ge && sValid[tid])
+                        for (int w = 0; w < NW; ++w) part[c] += (double)sRed[w][tid];
+                    __syncthreads();
+                }
+                if (tid >= gs && tid < ge && sValid[tid]) {
+                    float* out = (float*)P.out;
+                    for (int k = 0; k < P.n_zeta; ++k)
+                        out[k * P.out_stride + t0 + tid] =
+                            (float)(det.scale * (part[0] + (double)P.psb_c2z[k] * part[1] - (double)P.psb_s2z[k] * part[2]));
+                }
+            }
         }
 
         if (tid < ns && !sValid[tid]) {
             if (MODE == kForward) ((float*)P.out)[t0 + tid] = __int_as_float(0x7fc00000);
+            if (MODE == kPsb)
+                for (int k = 0; k < P.n_zeta; ++k) ((float*)P.out)[k * P.out_stride + t0 + tid] = __int_as_float(0x7fc00000);
             if (MODE == kCount) P.counts[t0 + tid] = -1;
         }
         __syncthreads();
@@ -544,6 +582,14 @@ template <int S, int NP, int FETCH>
 static cudaError_t launch_s(const LaunchParams& p, int mode, cudaStream_t s) {
     if (p.total_tiles <= 0) return cudaSuccess;
     const unsigned grid = (unsigned)min(p.total_tiles, (long long)INT_MAX);
+    if (mode == kPsb) {
+        // three accumulators per sample: instantiated for beam cells only
+        if constexpr (FETCH == PISCO_FETCH_CELLS) {
+            k_fast<S, NP, PISCO_FETCH_CELLS, kPsb><<<grid, NT, 0, s>>>(p);
+            return cudaGetLastError();
+        }
+        return cudaErrorInvalidValue;
+    }
     switch (mode) {
         case kForward: k_fast<S, NP, FETCH, kForward><<<grid, NT, 0, s>>>(p); break;
         case kAdjoint: k_fast<S, NP, FETCH, kAdjoint><<<grid, NT, 0, s>>>(p); break;

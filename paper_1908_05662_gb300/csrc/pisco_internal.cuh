@@ -39,7 +39,9 @@ struct DetEntry {
 
 constexpr int kMaxDetPerLaunch = 64;
 
-enum Mode { kForward = 0, kAdjoint = 1, kCount = 2, kGrid = 3 };
+enum Mode { kForward = 0, kAdjoint = 1, kCount = 2, kGrid = 3, kPsb = 4 };
+
+constexpr int kMaxPsb = 8;  // polarisation angles per shared-geometry pass
 
 // Parameters of the FP32 tile kernel and of the FP64 plain kernel (by value).
 struct LaunchParams {
@@ -63,6 +65,9 @@ struct LaunchParams {
     int32_t* counts;       // count mode output
     int* err;
     int n_real;            // multi-realization plans: realizations per pixel
+    int n_zeta;            // shared-geometry pass: number of polarisation angles
+    long long out_stride;  // shared-geometry pass: elements between the TODs of two angles
+    float psb_c2z[kMaxPsb], psb_s2z[kMaxPsb];  // cos, sin of 2 (zeta_k - zeta of the plan's detector)
     int ndet;
     long long total_tiles;
     DetEntry det[kMaxDetPerLaunch];
@@ -104,6 +109,21 @@ struct pisco_plan {
 };
 
 namespace pisco {
+
+// Polarisation angles of a shared-geometry pass, as rotations relative to the plan detector's zeta.
+struct PsbAngles {
+    int n;
+    long long stride;  // elements between the TODs of two angles
+    float c2z[kMaxPsb], s2z[kMaxPsb];
+};
+
+// Host helpers shared by the API translation units (defined in pisco_api.cu).
+bool is_device_ptr(const void* p);
+pisco_status check_pointing(pisco_plan* plan, int64_t n, const double* a, const double* b, const double* c);
+// Launch one path over detectors [d0, d0 + nd) with per-detector sample ranges.
+pisco_status run(pisco_plan* plan, int mode, int d0, int nd, const int64_t* begin, const int64_t* count,
+                 const double* theta, const double* phi, const double* psi, void* out, const void* tod_in,
+                 int32_t* counts, cudaStream_t s, const PsbAngles* psb = nullptr);
 
 // Launchers (defined in the kernel translation units).
 cudaError_t launch_fast_texture(const LaunchParams& p, int mode, int tile_samples, int np, cudaStream_t s);

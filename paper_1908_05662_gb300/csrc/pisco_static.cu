@@ -17,14 +17,6 @@
 #include <cmath>
 #include <mutex>
 
-namespace pisco {
-bool is_device_ptr(const void* p);
-pisco_status check_pointing(pisco_plan* plan, int64_t n, const double* a, const double* b, const double* c);
-pisco_status run(pisco_plan* plan, int mode, int d0, int nd, const int64_t* begin, const int64_t* count,
-                 const double* theta, const double* phi, const double* psi, void* out, const void* tod_in,
-                 int32_t* counts, cudaStream_t s);
-}  // namespace pisco
-
 using namespace pisco;
 
 namespace {

@@ -26,7 +26,7 @@ STATUS_NAMES = {0: "PISCO_OK", 1: "PISCO_EINVAL", 2: "PISCO_ENOMEM", 3: "PISCO_E
 EXPORTS = ("pisco_plan_create", "pisco_plan_destroy", "pisco_last_error", "pisco_plan_omega",
            "pisco_convolve", "pisco_convolve_batched", "pisco_adjoint", "pisco_disc_count",
            "pisco_convolve_host", "pisco_sync_status", "pisco_beam_grid_adjoint", "pisco_omega_adjoint",
-           "pisco_update_beams", "pisco_beam_grid_adjoint_static")
+           "pisco_update_beams", "pisco_beam_grid_adjoint_static", "pisco_convolve_psb")
 
 
 class PiscoError(RuntimeError):
@@ -73,6 +73,7 @@ def load_library(path=LIB_PATH):
         "pisco_omega_adjoint": (c_int, [vp, c_int, i64, vp, vp, vp, vp]),
         "pisco_update_beams": (c_int, [vp, vp, ctypes.POINTER(dbl), vp]),
         "pisco_beam_grid_adjoint_static": (c_int, [vp, c_int, i64, vp, vp, vp, vp, vp, c_int, vp]),
+        "pisco_convolve_psb": (c_int, [vp, c_int, i64, vp, vp, vp, c_int, ctypes.POINTER(dbl), vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -162,6 +163,15 @@ def pisco_convolve_batched(plan, offsets, theta, phi, psi, tod):
     off = (ctypes.c_int64 * len(offsets))(*map(int, offsets))
     _check(load_library().pisco_convolve_batched(plan, n_det, off, _ptr(_f64(theta)), _ptr(_f64(phi)),
                                                  _ptr(_f64(psi)), _ptr(tod), _stream()), plan)
+    return tod
+
+
+def pisco_convolve_psb(plan, det, theta, phi, psi, zeta, tod):
+    """TODs (len(zeta), n) of detector det's beam at polarisation angles zeta (radians)."""
+    n = theta.numel()
+    z = (ctypes.c_double * len(zeta))(*map(float, zeta))
+    _check(load_library().pisco_convolve_psb(plan, det, n, _ptr(_f64(theta)), _ptr(_f64(phi)),
+                                             _ptr(_f64(psi)), len(zeta), z, _ptr(tod), _stream()), plan)
     return tod
 
 
@@ -257,6 +267,12 @@ class Plan:
         if out is None:
             out = torch.empty(self._out_shape(theta.numel()), dtype=self.out_dtype, device=theta.device)
         return pisco_convolve_batched(self.handle, offsets, theta, phi, psi, out)
+
+    def convolve_psb(self, theta, phi, psi, zeta, det=0, out=None):
+        """One pass for detectors sharing det's beam, eps and s at angles zeta: (len(zeta), n) float32."""
+        if out is None:
+            out = torch.empty(len(zeta), theta.numel(), dtype=torch.float32, device=theta.device)
+        return pisco_convolve_psb(self.handle, det, theta, phi, psi, zeta, out)
 
     def adjoint(self, theta, phi, psi, tod, det=0, maps=None, accumulate=False):
         if maps is None:
