@@ -67,3 +67,27 @@ def omega_tilde(b_tt, radius):
     uu, vv = np.meshgrid(u, u, indexing="xy")  # [j][i] -> (u_i, v_j)
     jac = 1.0 / np.sqrt(1.0 - uu * uu - vv * vv)
     return float(h * h * np.sum(w[:, None] * w[None, :] * b_tt * jac))
+
+
+def grid_from_healpix(maps, nside_b, radius, n):
+    """Tangent-plane grids (..., n, n) of beam maps given as HEALPix RING maps (..., 12 nside_b^2).
+
+    The paper stores each beamsor element as a HEALPix map (Sec. 5.1, beam
+    NSIDE 4x the sky's in Sec. 5.3 and Sec. 6).  Reading: the beam centre is
+    the map's north pole and the antenna coordinates are its spherical
+    coordinates, rho = theta and sigma = phi, so sigma = 0 lies along theta'0
+    (u = sin rho cos sigma).  Node (u_i, v_j) takes the ring-wise bilinear
+    value (``healpix.interp_weights``) at rho = arcsin(sqrt(u^2 + v^2)),
+    sigma = atan2(v, u); nodes with u^2 + v^2 > 1 lie off the hemisphere and
+    are zero.
+    """
+    from . import healpix as hp
+    maps = np.asarray(maps, np.float64)
+    u = nodes(n, radius)
+    uu, vv = np.meshgrid(u, u, indexing="xy")  # [j][i] -> (u_i, v_j)
+    r2 = uu * uu + vv * vv
+    on = r2 <= 1.0
+    rho = np.arcsin(np.sqrt(np.where(on, r2, 0.0)))
+    sigma = np.arctan2(vv, uu)
+    vals = hp.interpolate(nside_b, maps, rho, sigma)
+    return np.where(on, vals, 0.0)

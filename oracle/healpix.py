@@ -162,3 +162,74 @@ def query_disc(nside, theta0, phi0, radius):
     if not out:
         return np.zeros(0, np.int64)
     return np.sort(np.concatenate(out))
+
+
+def ring_theta(nside):
+    """Colatitudes theta_i of rings i = 1 .. 4 nside - 1 (array index i - 1), increasing."""
+    t = ring_table(nside)
+    return np.arctan2(t["sin_theta"], t["z"])
+
+
+def interp_weights(nside, theta, phi):
+    """Four RING pixels and weights of the ring-wise bilinear interpolation at (theta, phi).
+
+    The paper re-pixelises HEALPix beam maps "via interpolation" (Sec. 4.2,
+    Sec. 5.1) without naming the scheme; this is the reading used here:
+
+    * on a ring, linear in phi between the two pixel centres that bracket phi
+      (the ring is periodic, so the pair may straddle phi = 0);
+    * between the rings i and i + 1 that bracket theta (theta_i <= theta <
+      theta_{i+1}), linear in theta between the two on-ring values;
+    * above the first ring (theta < theta_1) the value is extrapolated from
+      rings 1 and 2, quadratic in theta: with w = (theta^2 - theta_1^2) /
+      (theta_2^2 - theta_1^2) <= 0 it is (1 - w) ring_1 + w ring_2 (a smooth
+      map is even in theta near the pole, and a beam has its peak there: the
+      pole value is extrapolated, not averaged from ring 1); the south cap is
+      the mirror image with the last two rings and pi - theta.
+
+    Returns (pix, w), each of shape (4,) + shape(theta): two pixels on each
+    of two rings.  The weights sum to one; they are non-negative except in
+    the polar caps, where the farther ring's are <= 0.
+    """
+    theta = np.asarray(theta, np.float64)
+    phi = np.asarray(phi, np.float64)
+    shape = np.broadcast(theta, phi).shape
+    theta = np.broadcast_to(theta, shape).ravel()
+    phi = np.broadcast_to(phi, shape).ravel()
+    t = ring_table(nside)
+    th_r = ring_theta(nside)
+    nr = th_r.shape[0]
+    pix = np.zeros((4, theta.size), np.int64)
+    w = np.zeros((4, theta.size), np.float64)
+
+    def on_ring(r, ph):
+        """Two bracketing pixels of ring index r and their phi weights."""
+        cnt, dphi = t["count"][r], t["dphi"][r]
+        x = (ph - t["phi0"][r]) / dphi
+        j0 = np.floor(x)
+        f = x - j0
+        j0 = np.mod(j0.astype(np.int64), cnt)
+        j1 = np.mod(j0 + 1, cnt)
+        return t["first"][r] + j0, t["first"][r] + j1, 1.0 - f, f
+
+    for k in range(theta.size):
+        th, ph = theta[k], phi[k]
+        if th < th_r[0]:  # north cap: rings 1, 2
+            r, wt = 0, (th * th - th_r[0] ** 2) / (th_r[1] ** 2 - th_r[0] ** 2)
+        elif th >= th_r[-1]:  # south cap: the last two rings, mirrored
+            r, a, b, c = nr - 2, np.pi - th, np.pi - th_r[-1], np.pi - th_r[-2]
+            wt = 1.0 - (a * a - b * b) / (c * c - b * b)
+        else:
+            r = int(np.searchsorted(th_r, th, side="right")) - 1  # th_r[r] <= th < th_r[r + 1]
+            wt = (th - th_r[r]) / (th_r[r + 1] - th_r[r])
+        p0, p1, a0, a1 = on_ring(r, ph)
+        q0, q1, b0, b1 = on_ring(r + 1, ph)
+        pix[:, k] = [p0, p1, q0, q1]
+        w[:, k] = [(1 - wt) * a0, (1 - wt) * a1, wt * b0, wt * b1]
+    return pix.reshape((4,) + shape), w.reshape((4,) + shape)
+
+
+def interpolate(nside, m, theta, phi):
+    """Ring-wise bilinear value of map(s) m (..., Npix) at (theta, phi) (``interp_weights``)."""
+    pix, w = interp_weights(nside, theta, phi)
+    return np.sum(np.asarray(m, np.float64)[..., pix] * w, axis=-pix.ndim)
