@@ -126,6 +126,28 @@ pisco_status pisco_plan_create(pisco_plan** out, int nside, double radius_rad,
                                const double* omega_tilde,
                                const pisco_options* opt, void* stream);
 
+/*
+ * pisco_beam_grids_from_healpix -- beamsor maps given as HEALPix RING maps (the
+ * paper's representation: Sec. 5.1, beam NSIDE 4x the sky's in Sec. 5.3 and
+ * Sec. 6) resampled onto the tangent-plane grid that pisco_plan_create takes.
+ * The beam centre is the maps' north pole and (rho, sigma) are their (theta,
+ * phi); node (u_i, v_j), u_i = sin(R)(2i/(grid_n-1) - 1), takes the value at
+ * rho = asin(sqrt(u^2 + v^2)), sigma = atan2(v, u) by ring-wise bilinear
+ * interpolation (the paper interpolates without naming a scheme, Sec. 4.2):
+ * linear in phi along a ring, linear in theta between rings, quadratic in
+ * theta from rings 1 and 2 above ring 1.  Nodes with u^2 + v^2 > 1 are zero.
+ *   nside_b     HEALPix resolution of the beam maps, 1 <= nside_b <= 8192.
+ *   n_maps      number of maps (6 per detector, ordered as beam_grids).
+ *   maps        device float32 [n_maps][12 nside_b^2], RING order.
+ *   radius_rad  grid radius R, 0 < R < pi/2 (the plan's radius).
+ *   grid_n      nodes per grid side, 2 <= grid_n <= 4096.
+ *   grids       device float32 [n_maps][grid_n][grid_n]; overwritten.
+ * FP64 arithmetic, one thread per node, no allocation; errors as for
+ * pisco_plan_create (pisco_last_error(NULL)).
+ */
+pisco_status pisco_beam_grids_from_healpix(int nside_b, int n_maps, const float* maps, double radius_rad,
+                                           int grid_n, float* grids, void* stream);
+
 /* Free a plan and its device memory (synchronises the device first).  NULL is a no-op. */
 void pisco_plan_destroy(pisco_plan* plan);
 

@@ -22,22 +22,40 @@ import torch
 FWHM_TO_SIGMA = 1.0 / math.sqrt(8.0 * math.log(2.0))
 
 
-def gaussian_beam_grids(n, radius, fwhm_deg, ellipticity=0.0, xpol=0.0, sidelobe=None, ideal=False,
-                        device="cpu", dtype=torch.float64):
-    """(6, n, n) maps TT, QT, UT, TQ, QQ, UQ of the parametric beam."""
-    t = lambda x: torch.as_tensor(x, dtype=dtype, device=device)
-    u = math.sin(radius) * (2.0 * torch.arange(n, dtype=dtype, device=device) / (n - 1) - 1.0)
-    vv, uu = torch.meshgrid(u, u, indexing="ij")  # [j][i] -> (u_i, v_j)
+def gaussian_beam_at(u, v, fwhm_deg, ellipticity=0.0, xpol=0.0, sidelobe=None, ideal=False):
+    """(6, ...) maps TT, QT, UT, TQ, QQ, UQ of the parametric beam at orthographic coordinates
+    u = sin(rho) cos(sigma), v = sin(rho) sin(sigma) (tensors of one shape)."""
+    t = lambda x: torch.as_tensor(x, dtype=u.dtype, device=u.device)
     s = torch.deg2rad(t(fwhm_deg)) * FWHM_TO_SIGMA
     e = t(ellipticity)
     sx, sy = s * (1.0 + e), s * (1.0 - e)
-    g = torch.exp(-0.5 * ((uu / sx) ** 2 + (vv / sy) ** 2))
+    g = torch.exp(-0.5 * ((u / sx) ** 2 + (v / sy) ** 2))
     if sidelobe is not None:
         amp, c, w = sidelobe
-        rho = torch.asin(torch.clamp(torch.sqrt(uu * uu + vv * vv), max=1.0))
+        rho = torch.asin(torch.clamp(torch.sqrt(u * u + v * v), max=1.0))
         g = g + amp * torch.exp(-0.5 * ((rho - math.radians(c)) / math.radians(w)) ** 2)
     zero = torch.zeros_like(g)
     if ideal:
         return torch.stack([g, zero, zero, zero, g, zero])
     xp = t(xpol)
     return torch.stack([(1.0 + xp) * g, zero, zero, zero, (1.0 - xp) * g, zero])
+
+
+def gaussian_beam_grids(n, radius, fwhm_deg, ellipticity=0.0, xpol=0.0, sidelobe=None, ideal=False,
+                        device="cpu", dtype=torch.float64):
+    """(6, n, n) maps TT, QT, UT, TQ, QQ, UQ of the parametric beam."""
+    u = math.sin(radius) * (2.0 * torch.arange(n, dtype=dtype, device=device) / (n - 1) - 1.0)
+    vv, uu = torch.meshgrid(u, u, indexing="ij")  # [j][i] -> (u_i, v_j)
+    return gaussian_beam_at(uu, vv, fwhm_deg, ellipticity, xpol, sidelobe, ideal)
+
+
+def gaussian_beam_healpix(nside_b, fwhm_deg, ellipticity=0.0, xpol=0.0, sidelobe=None, ideal=False,
+                          device="cpu", dtype=torch.float64):
+    """(6, 12 nside_b^2) HEALPix RING maps of the same beam centred on the north pole, the
+    paper's beam representation: pixel (theta, phi) holds the beam at rho = theta, sigma = phi.
+    Pixels beyond the equator (rho > 90 deg) are zero."""
+    from .synthetic import healpix_centres
+    th, ph = (torch.as_tensor(a, dtype=dtype, device=device) for a in healpix_centres(nside_b))
+    st = torch.sin(th)
+    maps = gaussian_beam_at(st * torch.cos(ph), st * torch.sin(ph), fwhm_deg, ellipticity, xpol, sidelobe, ideal)
+    return torch.where(th <= 0.5 * math.pi, maps, torch.zeros_like(maps))

@@ -145,6 +145,44 @@ void set_error(pisco_plan* plan, const char* fmt, ...);
 
 namespace pisco {
 
+// Geometry of RING ring index r (0-based; ring number i = r + 1) of a map of the given nside.
+static __device__ __forceinline__ RingInfo make_ring(int r, int nside) {
+    const long long n = nside;
+    const long long i = r + 1;
+    RingInfo R;
+    double omz;
+    if (i < n) {
+        omz = (double)(i * i) / (3.0 * (double)(n * n));
+        R.z = 1.0 - omz;
+        R.count = (int)(4 * i);
+        R.dphi = kPi / (2.0 * (double)i);
+        R.phi0 = 0.5 * R.dphi;
+        R.first = 2 * i * (i - 1);
+    } else if (i <= 3 * n) {
+        R.z = 4.0 / 3.0 - 2.0 * (double)i / (3.0 * (double)n);
+        omz = 1.0 - R.z;
+        R.count = (int)(4 * n);
+        R.dphi = kPi / (2.0 * (double)n);
+        R.phi0 = 0.5 * (double)((i - n + 1) % 2) * R.dphi;
+        R.first = 2 * n * (n - 1) + (i - n) * 4 * n;
+    } else {
+        const long long m = 4 * n - i;
+        double opz = (double)(m * m) / (3.0 * (double)(n * n));
+        R.z = -(1.0 - opz);
+        omz = 1.0 - R.z;
+        R.count = (int)(4 * m);
+        R.dphi = kPi / (2.0 * (double)m);
+        R.phi0 = 0.5 * R.dphi;
+        R.first = 12 * n * n - 2 * m * (m + 1);
+    }
+    R.s = sqrt(omz * (1.0 + R.z));
+    R.theta = atan2(R.s, R.z);
+    R.s_f = (float)R.s;
+    R.inv_s2_f = (float)(1.0 / (R.s * R.s));
+    R.dphi_f = (float)R.dphi;
+    return R;
+}
+
 // Continuous RING ring number (1-based) of colatitude cosine z (inverse of the
 // ring heights of Sec. 5.1's scheme); used to bound the rings a disc can meet.
 static __device__ __forceinline__ double ring_number(double z, int nside) {

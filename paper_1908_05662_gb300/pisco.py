@@ -26,7 +26,8 @@ STATUS_NAMES = {0: "PISCO_OK", 1: "PISCO_EINVAL", 2: "PISCO_ENOMEM", 3: "PISCO_E
 EXPORTS = ("pisco_plan_create", "pisco_plan_destroy", "pisco_last_error", "pisco_plan_omega",
            "pisco_convolve", "pisco_convolve_batched", "pisco_adjoint", "pisco_disc_count",
            "pisco_convolve_host", "pisco_sync_status", "pisco_beam_grid_adjoint", "pisco_omega_adjoint",
-           "pisco_update_beams", "pisco_beam_grid_adjoint_static", "pisco_convolve_psb")
+           "pisco_update_beams", "pisco_beam_grid_adjoint_static", "pisco_convolve_psb",
+           "pisco_beam_grids_from_healpix")
 
 
 class PiscoError(RuntimeError):
@@ -74,6 +75,7 @@ def load_library(path=LIB_PATH):
         "pisco_update_beams": (c_int, [vp, vp, ctypes.POINTER(dbl), vp]),
         "pisco_beam_grid_adjoint_static": (c_int, [vp, c_int, i64, vp, vp, vp, vp, vp, c_int, vp]),
         "pisco_convolve_psb": (c_int, [vp, c_int, i64, vp, vp, vp, c_int, ctypes.POINTER(dbl), vp, vp]),
+        "pisco_beam_grids_from_healpix": (c_int, [c_int, c_int, vp, dbl, c_int, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -164,6 +166,23 @@ def pisco_convolve_batched(plan, offsets, theta, phi, psi, tod):
     _check(load_library().pisco_convolve_batched(plan, n_det, off, _ptr(_f64(theta)), _ptr(_f64(phi)),
                                                  _ptr(_f64(psi)), _ptr(tod), _stream()), plan)
     return tod
+
+
+def pisco_beam_grids_from_healpix(maps, nside_b, radius, grid_n, grids=None):
+    """Tangent-plane grids (..., grid_n, grid_n) float32 of HEALPix beam maps (..., 12 nside_b^2)."""
+    if maps.dtype != torch.float32 or not maps.is_cuda:
+        raise ValueError("maps must be a float32 CUDA tensor")
+    maps = maps.contiguous()
+    npix = 12 * nside_b * nside_b
+    if maps.shape[-1] != npix:
+        raise ValueError(f"maps must have last dimension 12 nside_b^2 = {npix}")
+    lead = tuple(maps.shape[:-1])
+    n_maps = maps.numel() // npix
+    if grids is None:
+        grids = torch.empty(lead + (grid_n, grid_n), dtype=torch.float32, device=maps.device)
+    _check(load_library().pisco_beam_grids_from_healpix(int(nside_b), n_maps, _ptr(maps), float(radius),
+                                                        int(grid_n), _ptr(grids), _stream()))
+    return grids
 
 
 def pisco_convolve_psb(plan, det, theta, phi, psi, zeta, tod):

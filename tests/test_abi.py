@@ -58,3 +58,14 @@ def test_calls_on_a_null_plan_are_rejected(lib):
     assert lib.pisco_disc_count(None, 0, None, None, None, None) == pisco.PISCO_EINVAL
     assert lib.pisco_sync_status(None, None) == pisco.PISCO_EINVAL
     lib.pisco_plan_destroy(None)
+    z = (ctypes.c_double * 2)(0.0, 1.0)
+    assert lib.pisco_convolve_psb(None, 0, 0, None, None, None, 2, z, None, None) == pisco.PISCO_EINVAL
+
+
+def test_healpix_beam_resampling_rejects_bad_arguments_before_touching_the_device(lib):
+    p = ctypes.c_void_p(16)
+    for nside_b, n_maps, radius, grid_n in [(0, 6, 0.1, 11), (9000, 6, 0.1, 11), (4, 0, 0.1, 11),
+                                           (4, 6, 0.0, 11), (4, 6, 1.6, 11), (4, 6, 0.1, 1), (4, 6, 0.1, 5000)]:
+        st = lib.pisco_beam_grids_from_healpix(nside_b, n_maps, p, radius, grid_n, p, None)
+        assert st == pisco.PISCO_EINVAL
+        assert lib.pisco_last_error(None)
