@@ -148,6 +148,47 @@ pisco_status pisco_plan_create(pisco_plan** out, int nside, double radius_rad,
 pisco_status pisco_beam_grids_from_healpix(int nside_b, int n_maps, const float* maps, double radius_rad,
                                            int grid_n, float* grids, void* stream);
 
+/*
+ * Map-making (Sec. 5.1: TOD go on to "a map-making code"; Sec. 6 makes maps
+ * from PISCO TOD of pixels observed at their centres at three angles).  The
+ * paper names no map-maker; these calls are the binned (naive) one:
+ * per-pixel least squares with the pointing matrix of a delta beam at the
+ * boresight, a_t = s/2 [(1 + eps), (1 - eps) cos 2 chi_t, (1 - eps) sin 2 chi_t]
+ * (eq. M_pol), chi_t = psi_t + zeta (Appendix A at rho = 0), pixel = the RING
+ * pixel containing (theta_t, phi_t) (Gorski et al. 2005).
+ *
+ * pisco_ang2pix -- RING pixel of each direction.
+ *   theta, phi  device float64 [n]; pix device int64 [n], -1 for non-finite
+ *               angles or theta outside [0, pi].
+ *
+ * pisco_map_accumulate -- adds one detector's samples to the per-pixel normal
+ * equations acc, device float64 [10][12 nside^2] laid out as
+ *   acc[0..5]  sum a a^T   (II, IQ, IU, QQ, QU, UU)
+ *   acc[6..8]  sum a d     (I, Q, U)
+ *   acc[9]     hits.
+ *   det         host pointer to the detector (zeta, eps, s_resp).
+ *   tod         device [n] of tod_dtype (PISCO_DTYPE_F32 or PISCO_DTYPE_F64).
+ *   accumulate  0: acc is zeroed first; otherwise the samples are added (call
+ *               once per detector to bin a focal plane).
+ * Samples with non-finite angles or data, or theta outside [0, pi], are
+ * skipped.  FP64 atomic adds: the summation order, hence the last bits, vary
+ * from run to run.
+ *
+ * pisco_map_solve -- maps, device float64 [3][12 nside^2] (I, Q, U): per
+ * pixel, m = (sum a a^T)^-1 sum a d where hits >= 3 and the reciprocal
+ * condition number lambda_min / lambda_max >= rcond_min (in [0, 1]); NaN
+ * elsewhere.  Hits are acc[9].
+ *
+ * All three take 1 <= nside <= 8192 and report argument errors through
+ * pisco_last_error(NULL).
+ */
+pisco_status pisco_ang2pix(int nside, int64_t n, const double* theta, const double* phi, int64_t* pix,
+                           void* stream);
+pisco_status pisco_map_accumulate(int nside, int64_t n, const double* theta, const double* phi,
+                                  const double* psi, const pisco_detector* det, const void* tod,
+                                  int tod_dtype, double* acc, int accumulate, void* stream);
+pisco_status pisco_map_solve(int nside, const double* acc, double rcond_min, double* maps, void* stream);
+
 /* Free a plan and its device memory (synchronises the device first).  NULL is a no-op. */
 void pisco_plan_destroy(pisco_plan* plan);
 

@@ -27,7 +27,7 @@ EXPORTS = ("pisco_plan_create", "pisco_plan_destroy", "pisco_last_error", "pisco
            "pisco_convolve", "pisco_convolve_batched", "pisco_adjoint", "pisco_disc_count",
            "pisco_convolve_host", "pisco_sync_status", "pisco_beam_grid_adjoint", "pisco_omega_adjoint",
            "pisco_update_beams", "pisco_beam_grid_adjoint_static", "pisco_convolve_psb",
-           "pisco_beam_grids_from_healpix")
+           "pisco_beam_grids_from_healpix", "pisco_ang2pix", "pisco_map_accumulate", "pisco_map_solve")
 
 
 class PiscoError(RuntimeError):
@@ -76,6 +76,10 @@ def load_library(path=LIB_PATH):
         "pisco_beam_grid_adjoint_static": (c_int, [vp, c_int, i64, vp, vp, vp, vp, vp, c_int, vp]),
         "pisco_convolve_psb": (c_int, [vp, c_int, i64, vp, vp, vp, c_int, ctypes.POINTER(dbl), vp, vp]),
         "pisco_beam_grids_from_healpix": (c_int, [c_int, c_int, vp, dbl, c_int, vp, vp]),
+        "pisco_ang2pix": (c_int, [c_int, i64, vp, vp, vp, vp]),
+        "pisco_map_accumulate": (c_int, [c_int, i64, vp, vp, vp, ctypes.POINTER(pisco_detector), vp, c_int, vp,
+                                         c_int, vp]),
+        "pisco_map_solve": (c_int, [c_int, vp, dbl, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -183,6 +187,43 @@ def pisco_beam_grids_from_healpix(maps, nside_b, radius, grid_n, grids=None):
     _check(load_library().pisco_beam_grids_from_healpix(int(nside_b), n_maps, _ptr(maps), float(radius),
                                                         int(grid_n), _ptr(grids), _stream()))
     return grids
+
+
+def pisco_ang2pix(nside, theta, phi, pix=None):
+    """RING pixel (int64, -1 for invalid angles) of each direction."""
+    if pix is None:
+        pix = torch.empty(theta.numel(), dtype=torch.int64, device=theta.device)
+    _check(load_library().pisco_ang2pix(int(nside), theta.numel(), _ptr(_f64(theta)), _ptr(_f64(phi)), _ptr(pix),
+                                        _stream()))
+    return pix
+
+
+def pisco_map_accumulate(nside, theta, phi, psi, det, tod, acc=None, accumulate=False):
+    """Per-pixel normal equations acc (10, 12 nside^2) float64 of one detector's TOD (float32/64)."""
+    if acc is None:
+        acc = torch.empty(10, 12 * nside * nside, dtype=torch.float64, device=theta.device)
+    if tod.dtype not in (torch.float32, torch.float64) or not tod.is_cuda or not tod.is_contiguous():
+        raise ValueError("tod must be a contiguous float32/float64 CUDA tensor")
+    d = pisco_detector(*map(float, det))
+    code = PISCO_DTYPE_F32 if tod.dtype == torch.float32 else PISCO_DTYPE_F64
+    _check(load_library().pisco_map_accumulate(int(nside), theta.numel(), _ptr(_f64(theta)), _ptr(_f64(phi)),
+                                               _ptr(_f64(psi)), ctypes.byref(d), _ptr(tod), code, _ptr(acc),
+                                               int(bool(accumulate)), _stream()))
+    return acc
+
+
+def pisco_map_solve(nside, acc, rcond_min=1e-6, maps=None):
+    """Binned I, Q, U maps (3, 12 nside^2) float64 from the normal equations (NaN where unsolved)."""
+    if maps is None:
+        maps = torch.empty(3, 12 * nside * nside, dtype=torch.float64, device=acc.device)
+    _check(load_library().pisco_map_solve(int(nside), _ptr(acc), float(rcond_min), _ptr(maps), _stream()))
+    return maps
+
+
+def binned_map(nside, theta, phi, psi, det, tod, rcond_min=1e-6):
+    """(maps (3, Npix) float64, hits (Npix,) int64) of one detector's TOD."""
+    acc = pisco_map_accumulate(nside, theta, phi, psi, det, tod)
+    return pisco_map_solve(nside, acc, rcond_min), acc[9].round().to(torch.int64)
 
 
 def pisco_convolve_psb(plan, det, theta, phi, psi, zeta, tod):
