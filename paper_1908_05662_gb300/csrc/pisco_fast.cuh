@@ -107,8 +107,15 @@ static __device__ __forceinline__ float4 ld_nc_v4(const float* p) {
     return a;
 }
 
+// Resident CTAs per SM the register allocation targets, per mode (measured on the
+// single-detector workload, 16-sample tiles): 3 (80 registers, a few spilled to
+// L1) runs the forward and sky-adjoint passes 10 % faster than 2 (128 registers);
+// the shared-geometry pass keeps three accumulators per sample and is fastest at
+// 2; the beam-grid transpose, bound by its atomic adds, at 4.
+constexpr int fast_min_blocks(int mode) { return mode == kPsb ? 2 : (mode == kGrid ? 4 : 3); }
+
 template <int S, int NP, int FETCH, int MODE>
-__global__ void __launch_bounds__(NT, 2) k_fast(const __grid_constant__ LaunchParams P) {
+__global__ void __launch_bounds__(NT, fast_min_blocks(MODE)) k_fast(const __grid_constant__ LaunchParams P) {
     __shared__ double sTh[S], sPh[S], sPx[S], sPy[S], sPz[S];
     __shared__ float4 sA[S];  // cos(b/2), sin(b/2), cos psi0, sin psi0   (b = phi0 - phi_c)
     __shared__ float4 sB[S];  // cos theta0, sin theta0, Z_theta, Z_phi
