@@ -64,10 +64,10 @@ def parse():
     ap.add_argument("--samples", type=int, default=WORKLOAD["n_samples"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline leg")
     ap.add_argument("--workload", default="single",
-                    choices=["single", "focalplane", "multireal", "table1", "psb", "sec61"],
+                    choices=["single", "focalplane", "multireal", "table1", "psb", "sec61", "grad"],
                     help="single: the default single-detector line; the others measure the focal-plane, "
                          "multi-realization, Table 1 replica, PSB-pair (shared geometry) and Sec. 6.1 "
-                         "(TOD then binned maps) configurations")
+                         "(TOD then binned maps) configurations, and grad: the differentiation configuration")
     return ap.parse_args()
 
 
@@ -457,6 +457,94 @@ def run_sec61(args, dev):
     print(json.dumps(out))
 
 
+def run_grad(args, dev):
+    """The differentiation configuration: nside-512 FP32 sky, one detector with the parametric beam
+    (FWHM 1.5 deg, ellipticity 0.05, cross-polar leakage 0.005) on a 201^2 grid of radius 5 deg, 1e7
+    samples of the azimuth scan.  One step = beam grids from the parameters, TOD (pisco_convolve
+    through PiscoConvolve), chi^2 against the TOD of perturbed parameters (1.52, 0.06, 0.004), and
+    its backward pass: the sky adjoint (TOD -> I, Q, U maps), the beam-grid adjoint, the Omega~ term
+    and the chain to d chi^2 / d(FWHM, e, l).  The gradient is checked on a 48-sample slice against
+    central differences (h = 1e-4) of the FP64 oracle."""
+    from oracle import beam as ob
+    from oracle import convolve as oc
+    from paper_1908_05662_gb300 import autograd as pag
+    nside, r, n_grid = 512, math.radians(5.0), 201
+    n = args.samples
+    sky = cached_sky(nside, 1, dev)
+    th, ph, ps = (a.contiguous() for a in sy.ces_scan(n, device=dev))
+    det = (0.0, 0.0, 1.0)
+    p0, pt = (1.5, 0.05, 0.005), (1.52, 0.06, 0.004)
+
+    def tod_of(p, sky_t, theta, phi, psi):
+        g = beams.gaussian_beam_grids(n_grid, r, p[0], p[1], p[2], device=dev)
+        return pag.convolve(sky_t, g, theta, phi, psi, nside, r, det)
+
+    with torch.no_grad():
+        target = tod_of(torch.tensor(pt, dtype=torch.float64, device=dev), sky, th, ph, ps).double()
+
+    def step():
+        params = torch.tensor(p0, dtype=torch.float64, device=dev, requires_grad=True)
+        sky_t = sky.clone().requires_grad_(True)
+        loss = ((tod_of(params, sky_t, th, ph, ps).double() - target) ** 2).sum()
+        loss.backward()
+        return params.grad, sky_t.grad
+
+    stream = torch.cuda.current_stream()
+    with ClockSampler(torch.cuda.current_device()) as clocks:
+        ms = _event_time(step, args.steps, args.warmup, stream)
+    # the passes one by one on the same inputs
+    g = beams.gaussian_beam_grids(n_grid, r, *p0, device=dev).float()[None].contiguous()
+    y = torch.randn(n, device=dev)
+    with pisco.Plan(nside, r, sky, [det], g) as plan:
+        tod = plan.convolve(th, ph, ps)
+        parts = {"forward_ms": _event_time(lambda: plan.convolve(th, ph, ps, out=tod), 2, 1, stream),
+                 "sky_adjoint_ms": _event_time(lambda: plan.adjoint(th, ph, ps, y), 2, 1, stream),
+                 "beam_grid_adjoint_ms": _event_time(lambda: plan.beam_grid_adjoint(th, ph, ps, y), 2, 1, stream)}
+        pairs = int(plan.disc_count(th, ph).to(torch.int64).sum().item())
+        plan.sync_status()
+    # gradient check on a slice against the FP64 oracle
+    # (the slice's target is the oracle's TOD of the perturbed parameters, on both sides)
+    k = 48
+    sl = slice(0, k)
+    skyn = sky.cpu().numpy()
+    thn, phn, psn = (a[sl].cpu().numpy() for a in (th, ph, ps))
+
+    def oracle_tod(p):
+        gr = beams.gaussian_beam_grids(n_grid, r, p[0], p[1], p[2]).numpy()
+        return oc.tod(nside, r, skyn, gr, det, ob.omega_tilde(gr[0], r), thn, phn, psn)
+
+    tgtn = oracle_tod(pt)
+    params = torch.tensor(p0, dtype=torch.float64, device=dev, requires_grad=True)
+    loss = ((tod_of(params, sky, th[sl], ph[sl], ps[sl]).double() - torch.as_tensor(tgtn, device=dev)) ** 2).sum()
+    loss.backward()
+    grad = params.grad.cpu().numpy()
+
+    def chi2(p):
+        return float(np.sum((oracle_tod(p) - tgtn) ** 2))
+
+    h = 1e-4
+    fd = []
+    for i in range(3):
+        e = np.zeros(3)
+        e[i] = h
+        fd.append((chi2(np.array(p0) + e) - chi2(np.array(p0) - e)) / (2 * h))
+    rel = [abs(grad[i] - fd[i]) / abs(fd[i]) for i in range(3)]
+    bg = parts["beam_grid_adjoint_ms"]
+    out = {"metric": "gradient steps/s (TOD, chi^2, backward to sky maps and beam parameters; 1e7 samples)",
+           "value": 1e3 / ms, "unit": "steps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": ms, "samples_per_s": n / (ms / 1e3), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "differentiation: nside 512, parametric beam (FWHM 1.5 deg, e 0.05, l 0.005), "
+                                  "R 5 deg, 201^2 grid, 1e7 scan samples", "samples": n, "pairs_per_pass": pairs},
+           "passes": parts, "grad_vs_oracle_fd_rel": rel, "grad": list(map(float, grad)), "fd": fd,
+           "roofline": {"bound": "alu", "kernel": "pisco::k_fast<16, beam-grid transpose>",
+                        "achieved": FLOPS_PER_PAIR * pairs / (bg / 1e3) / 1e12, "peak": FP32_PEAK_TFLOPS,
+                        "unit": "TFLOP/s", "frac": FLOPS_PER_PAIR * pairs / (bg / 1e3) / 1e12 / FP32_PEAK_TFLOPS,
+                        "traffic": None, "note": "forward flops per pair as the work unit of the transpose"},
+           "gpu_launches": 9 * args.steps, "clocks": clocks.summary()}
+    print(json.dumps(out))
+
+
 def run_table1(args, dev):
     """The paper's Table 1 setup (Sec. 5.3.1): 2 detectors (zeta 0 and -90 deg) x 3 position angles
     (0, 45, 90 deg) x every nside-128 pixel centre = 1,179,648 samples, Gaussian FWHM 1.5 deg,
@@ -529,7 +617,7 @@ def main():
     if args.workload != "single":
         torch.cuda.set_device(local)
         {"focalplane": run_focalplane, "multireal": run_multireal, "table1": run_table1, "psb": run_psb,
-         "sec61": run_sec61}[args.workload](
+         "sec61": run_sec61, "grad": run_grad}[args.workload](
             args, torch.device("cuda", local))
         return
     torch.cuda.set_device(local)

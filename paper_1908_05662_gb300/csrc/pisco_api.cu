@@ -641,10 +641,9 @@ extern "C" pisco_status pisco_beam_grid_adjoint(pisco_plan* plan, int det, int64
     }
     cudaStream_t s = (cudaStream_t)stream;
     const int f64 = plan->precision == PISCO_FP64_PLAIN;
-    const size_t elem = f64 ? sizeof(double) : sizeof(float);
-    const size_t nn = (size_t)plan->grid_n * plan->grid_n;
-    if (!plan->d_gscratch) PISCO_CUDA(plan, cudaMalloc(&plan->d_gscratch, 3 * nn * elem));
-    PISCO_CUDA(plan, cudaMemsetAsync(plan->d_gscratch, 0, 3 * nn * elem, s));
+    const size_t bytes = folded_grad_bytes(plan->grid_n, f64);
+    if (!plan->d_gscratch) PISCO_CUDA(plan, cudaMalloc(&plan->d_gscratch, bytes));
+    PISCO_CUDA(plan, cudaMemsetAsync(plan->d_gscratch, 0, bytes, s));
     if (n > 0) {
         const int64_t begin = 0, count = n;
         st = run(plan, kGrid, det, 1, &begin, &count, theta, phi, psi, plan->d_gscratch, tod, nullptr, s);

@@ -66,20 +66,23 @@ static __device__ __forceinline__ float rcp_approx(float x) {
 }
 
 // Add the 12 accumulated node gradients of one cell (maps A, Bq', Cu' x nodes
-// (i, j), (i+1, j), (i, j+1), (i+1, j+1)) to the folded gradient [3][N][N]
-// and clear them.
+// (i, j), (i+1, j), (i, j+1), (i+1, j+1)) to the folded gradient and clear them.
+// The FP32 folded gradient is interleaved per node, [N][N][4] = (A, Bq', Cu', 0),
+// so each node takes one 16-byte vector reduction instead of three scalar atomics.
+static __device__ __forceinline__ void red_add_v4(float* p, float a, float b, float c) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(0.f)
+                 : "memory");
+}
+
 static __device__ __forceinline__ void flush_grid(float* g, int cell, int nc, int n, float* gw) {
     const int i = cell % nc, j = cell / nc;
-    const long long nn = (long long)n * n;
     const long long base = (long long)j * n + i;
     const long long off[4] = {base, base + 1, base + n, base + n + 1};
 #pragma unroll
-    for (int m = 0; m < 3; ++m)
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            if (gw[4 * m + k] != 0.f) atomicAdd(g + m * nn + off[k], gw[4 * m + k]);
-            gw[4 * m + k] = 0.f;
-        }
+    for (int k = 0; k < 4; ++k) {
+        if (gw[k] != 0.f || gw[4 + k] != 0.f || gw[8 + k] != 0.f) red_add_v4(g + 4 * off[k], gw[k], gw[4 + k], gw[8 + k]);
+        gw[k] = gw[4 + k] = gw[8 + k] = 0.f;
+    }
 }
 
 // Bilinear value from a 2 x 2 texel gather, whose components are the nodes

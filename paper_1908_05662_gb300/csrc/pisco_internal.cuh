@@ -125,6 +125,12 @@ pisco_status run(pisco_plan* plan, int mode, int d0, int nd, const int64_t* begi
                  const double* theta, const double* phi, const double* psi, void* out, const void* tod_in,
                  int32_t* counts, cudaStream_t s, const PsbAngles* psb = nullptr);
 
+// Bytes of the folded beam-grid gradient scratch: FP32 plans interleave the three
+// folded maps per node with a pad ([N][N][4] floats), the plain path keeps [3][N][N] doubles.
+inline size_t folded_grad_bytes(int grid_n, int f64) {
+    return (size_t)grid_n * grid_n * (f64 ? 3 * sizeof(double) : 4 * sizeof(float));
+}
+
 // Launchers (defined in the kernel translation units).
 cudaError_t launch_fast_texture(const LaunchParams& p, int mode, int tile_samples, int np, cudaStream_t s);
 cudaError_t launch_fast_cells(const LaunchParams& p, int mode, int tile_samples, int np, cudaStream_t s);

@@ -150,7 +150,11 @@ __global__ void k_unfold(const T* __restrict__ f, int n, double eps, double zeta
     if (idx >= nn) return;
     double s2z, c2z;
     sincos(2.0 * zeta, &s2z, &c2z);
-    const double ga = f[idx], gbp = f[nn + idx], gcp = f[2 * nn + idx];
+    // FP32 folded gradients are interleaved per node ([N][N][4]), FP64 ones are [3][N][N]
+    const bool inter = sizeof(T) == sizeof(float);
+    const double ga = inter ? f[4 * idx] : f[idx];
+    const double gbp = inter ? f[4 * idx + 1] : f[nn + idx];
+    const double gcp = inter ? f[4 * idx + 2] : f[2 * nn + idx];
     const double gbq = c2z * gbp + s2z * gcp;   // transpose of the 2 zeta rotation
     const double gcu = -s2z * gbp + c2z * gcp;
     const double v[6] = {(1.0 + eps) * ga, (1.0 + eps) * gbq, (1.0 + eps) * gcu,   // TT, QT, UT

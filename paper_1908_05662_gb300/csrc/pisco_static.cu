@@ -26,6 +26,8 @@ constexpr int kStaticMaxGridN = 512;
 constexpr size_t kStaticScratchBytes = 3ull * kStaticMaxGridN * kStaticMaxGridN * sizeof(double);
 
 __device__ __align__(256) unsigned char g_grid_scratch[kStaticScratchBytes];
+static_assert(kStaticScratchBytes >= 4ull * kStaticMaxGridN * kStaticMaxGridN * sizeof(float),
+              "the static scratch holds the interleaved FP32 folded gradient too");
 
 constexpr int kMaxDevices = 64;
 void* g_scratch_addr[kMaxDevices];
@@ -78,7 +80,7 @@ extern "C" pisco_status pisco_beam_grid_adjoint_static(pisco_plan* plan, int det
     }
     cudaStream_t s = (cudaStream_t)stream;
     const int f64 = plan->precision == PISCO_FP64_PLAIN;
-    const size_t bytes = 3ull * plan->grid_n * plan->grid_n * (f64 ? sizeof(double) : sizeof(float));
+    const size_t bytes = folded_grad_bytes(plan->grid_n, f64);
     e = cudaMemsetAsync(scratch, 0, bytes, s);
     if (e != cudaSuccess) {
         set_error(plan, "clearing the static scratch failed: %s", cudaGetErrorString(e));
