@@ -341,6 +341,28 @@ pisco_status pisco_convolve_host(pisco_plan* plan, int det, int64_t n,
                                  const double* h_theta, const double* h_phi,
                                  const double* h_psi, void* h_tod);
 
+/*
+ * pisco_plan_autotune -- chooses the FP32 kernel's tile shape for this plan.
+ * Sec. 5.2 fixes one block per pointing; here the shape (tile_samples in
+ * {8, 16, 32} consecutive samples per disc traversal x pixels_per_thread in
+ * {1, 2}) is a tuning choice whose best value depends on the scan and the
+ * disc size.  Every shape runs pisco_convolve on the n pointings given (a
+ * representative slice of the scan, e.g. 1e5 - 1e6 samples) once untimed and
+ * `reps` times timed with CUDA events on `stream`; the fastest is kept by the
+ * plan for its later calls.
+ *   tod_scratch        device float32 [n], overwritten (the TOD of the last shape tried).
+ *   reps               timed launches per shape, 1 .. 100.
+ *   tile_samples, pixels_per_thread, best_ms
+ *                      host outputs (each may be NULL): the chosen shape and its
+ *                      mean time per launch in milliseconds.
+ * Synchronises `stream`.  FP32 plans only (PISCO_EUNSUPPORTED otherwise); on
+ * error the plan keeps its previous shape.
+ */
+pisco_status pisco_plan_autotune(pisco_plan* plan, int det, int64_t n,
+                                 const double* theta, const double* phi, const double* psi,
+                                 void* tod_scratch, int reps, int* tile_samples,
+                                 int* pixels_per_thread, float* best_ms, void* stream);
+
 /* Synchronise the plan's work on `stream` and report any error a kernel
  * recorded since the last call (PISCO_EDEVICE), clearing it. */
 pisco_status pisco_sync_status(pisco_plan* plan, void* stream);

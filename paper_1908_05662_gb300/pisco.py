@@ -27,7 +27,8 @@ EXPORTS = ("pisco_plan_create", "pisco_plan_destroy", "pisco_last_error", "pisco
            "pisco_convolve", "pisco_convolve_batched", "pisco_adjoint", "pisco_disc_count",
            "pisco_convolve_host", "pisco_sync_status", "pisco_beam_grid_adjoint", "pisco_omega_adjoint",
            "pisco_update_beams", "pisco_beam_grid_adjoint_static", "pisco_convolve_psb",
-           "pisco_beam_grids_from_healpix", "pisco_ang2pix", "pisco_map_accumulate", "pisco_map_solve")
+           "pisco_beam_grids_from_healpix", "pisco_ang2pix", "pisco_map_accumulate", "pisco_map_solve",
+           "pisco_plan_autotune")
 
 
 class PiscoError(RuntimeError):
@@ -80,6 +81,8 @@ def load_library(path=LIB_PATH):
         "pisco_map_accumulate": (c_int, [c_int, i64, vp, vp, vp, ctypes.POINTER(pisco_detector), vp, c_int, vp,
                                          c_int, vp]),
         "pisco_map_solve": (c_int, [c_int, vp, dbl, vp, vp]),
+        "pisco_plan_autotune": (c_int, [vp, c_int, i64, vp, vp, vp, vp, c_int, ctypes.POINTER(c_int),
+                                        ctypes.POINTER(c_int), ctypes.POINTER(ctypes.c_float), vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -187,6 +190,17 @@ def pisco_beam_grids_from_healpix(maps, nside_b, radius, grid_n, grids=None):
     _check(load_library().pisco_beam_grids_from_healpix(int(nside_b), n_maps, _ptr(maps), float(radius),
                                                         int(grid_n), _ptr(grids), _stream()))
     return grids
+
+
+def pisco_plan_autotune(plan, det, theta, phi, psi, reps=2):
+    """Time the FP32 tile shapes on these pointings; the plan keeps the fastest.
+    Returns (tile_samples, pixels_per_thread, ms per launch)."""
+    scratch = torch.empty(theta.numel(), dtype=torch.float32, device=theta.device)
+    t, p, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
+    _check(load_library().pisco_plan_autotune(plan, det, theta.numel(), _ptr(_f64(theta)), _ptr(_f64(phi)),
+                                              _ptr(_f64(psi)), _ptr(scratch), int(reps), ctypes.byref(t),
+                                              ctypes.byref(p), ctypes.byref(ms), _stream()), plan)
+    return t.value, p.value, ms.value
 
 
 def pisco_ang2pix(nside, theta, phi, pix=None):
@@ -322,6 +336,10 @@ class Plan:
         if out is None:
             out = torch.empty(self._out_shape(theta.numel()), dtype=self.out_dtype, device=theta.device)
         return pisco_convolve(self.handle, det, theta, phi, psi, out)
+
+    def autotune(self, theta, phi, psi, det=0, reps=2):
+        """Pick the FP32 tile shape by timing it on these pointings: (tile_samples, pixels_per_thread, ms)."""
+        return pisco_plan_autotune(self.handle, det, theta, phi, psi, reps)
 
     def convolve_batched(self, offsets, theta, phi, psi, out=None):
         if out is None:
