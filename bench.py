@@ -678,6 +678,15 @@ def main():
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     e2e_value = n * world / e2e_s
 
+    # the same scan with packed 32-byte beam cells (FP32 values, int16 slopes), same tile shape
+    packed = pisco.Plan(WORKLOAD["nside"], r, sky, [det], g, precision=pisco.PISCO_FP32,
+                        beam_fetch=pisco.PISCO_FETCH_PACKED, tile_samples=tuned[0], pixels_per_thread=tuned[1])
+    tod_p = torch.empty(n, dtype=torch.float32, device=dev)
+    ms_packed = _event_time(lambda: packed.convolve(th, ph, ps, out=tod_p), args.steps, args.warmup, stream)
+    packed.sync_status()
+    packed.close()
+    packed_vs_cells = (tod_p.double() - tod.double()).abs().max().item() / tod.double().abs().max().item()
+
     # plain FP64 GPU path on a contiguous slice of the same scan
     n_plain = min(n, 100_000)
     plain = pisco.Plan(WORKLOAD["nside"], r, sky, [det], g, precision=pisco.PISCO_FP64_PLAIN)
@@ -717,6 +726,9 @@ def main():
                                "fp32_vs_fp64_normwise": fp32_vs_64},
             "gpu_launches": args.steps,
             "clocks": clocks.summary(),
+            "packed_cells": {"value": n_total / (ms_packed / 1e3), "unit": UNIT, "ms_per_step": ms_packed,
+                             "vs_cells_tod_normwise": packed_vs_cells,
+                             "note": "PISCO_FETCH_PACKED: 32-byte cells, FP32 values and int16 slopes"},
             "wall_s_timed": t_wall,
         }
         if not args.no_cpu:
@@ -726,6 +738,8 @@ def main():
             out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                                    "sample": f"first {k} consecutive samples of the scan (~15 s of CPU)"}
             out["err_vs_oracle_normwise"] = err
+            out["packed_cells"]["err_vs_oracle_normwise"] = (
+                np.max(np.abs(tod_p[:k].double().cpu().numpy() - ref)) / np.max(np.abs(ref)))
         print(json.dumps(out))
     plan.close()
     if world > 1:

@@ -85,14 +85,20 @@ typedef struct pisco_options {
     int precision;     /* PISCO_FP64_PLAIN or PISCO_FP32 */
     int tile_samples;       /* FP32 path: consecutive samples sharing one disc traversal: 8, 16 or 32 (0 = 16) */
     int pixels_per_thread;  /* FP32 path: consecutive ring pixels per thread: 1 or 2 (0 = 1) */
-    int beam_fetch;         /* FP32 path: PISCO_FETCH_CELLS or PISCO_FETCH_TEXTURE (0 = cells) */
+    int beam_fetch;         /* FP32 path: PISCO_FETCH_CELLS, _TEXTURE or _PACKED (0 = cells) */
     int n_real;             /* PISCO_*_MR plans: realizations, a multiple of 32 in [32, 256] */
 } pisco_options;
 
-/* How the FP32 kernel reads the beam (pisco_options.beam_fetch): 64-byte
- * bilinear-coefficient cells through L1/L2, or 2 x 2 texel gathers of the
- * folded node maps through the texture path.  Same arithmetic either way. */
-enum { PISCO_FETCH_TEXTURE = 1, PISCO_FETCH_CELLS = 2 };
+/* How the FP32 kernel reads the beam (pisco_options.beam_fetch):
+ *  PISCO_FETCH_CELLS    64-byte cells of FP32 bilinear coefficients through L1/L2;
+ *  PISCO_FETCH_TEXTURE  2 x 2 texel gathers of the folded node maps (same arithmetic);
+ *  PISCO_FETCH_PACKED   32-byte cells: per map the FP32 value at the cell's first
+ *                       node and the three bilinear slopes as int16 on a per-cell
+ *                       power-of-two scale (each slope within 2^-15 of the largest
+ *                       slope of its cell and map).  Half the bytes per pair of
+ *                       the FP32 cells; the plan fails with PISCO_EINVAL when the
+ *                       grid's slopes lie outside about 2^-80 .. 2^140. */
+enum { PISCO_FETCH_TEXTURE = 1, PISCO_FETCH_CELLS = 2, PISCO_FETCH_PACKED = 3 };
 
 typedef struct pisco_plan pisco_plan;  /* opaque, owned by the library */
 

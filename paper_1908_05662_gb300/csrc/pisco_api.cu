@@ -71,6 +71,23 @@ static void free_plan(pisco_plan* p) {
     delete p;
 }
 
+// Packed-cell plans: the encoder flags a grid whose slopes fall outside the
+// format's exponent range in word 2 of each detector's header (read after the
+// plan kernels have finished).
+static bool packed_range_ok(const pisco_plan* p, int* bad_det) {
+    if (p->precision != PISCO_FP32 || p->beam_fetch != PISCO_FETCH_PACKED) return true;
+    for (int d = 0; d < p->n_det; ++d) {
+        unsigned flag = 0;
+        if (cudaMemcpy(&flag, (const char*)p->d_beam + (size_t)d * p->beam_stride + 8, sizeof(unsigned),
+                       cudaMemcpyDeviceToHost) != cudaSuccess || flag != 0) {
+            cudaGetLastError();
+            *bad_det = d;
+            return false;
+        }
+    }
+    return true;
+}
+
 // Folded node maps A, Bq', Cu' of every detector as 2-D float textures
 // (created on first use, refilled by pisco_update_beams).
 static cudaError_t build_textures(pisco_plan* p, const float* beam_grids, cudaStream_t s) {
@@ -184,8 +201,9 @@ extern "C" pisco_status pisco_plan_create(pisco_plan** out, int nside, double ra
     }
     int fetch = opt && opt->beam_fetch ? opt->beam_fetch : PISCO_FETCH_CELLS;
     if (mr) fetch = PISCO_FETCH_CELLS;  // the multi-realization kernel reads coefficient cells
-    if (fetch != PISCO_FETCH_TEXTURE && fetch != PISCO_FETCH_CELLS) {
-        set_error(nullptr, "beam_fetch %d is not PISCO_FETCH_TEXTURE or PISCO_FETCH_CELLS", fetch);
+    if (fetch != PISCO_FETCH_TEXTURE && fetch != PISCO_FETCH_CELLS && fetch != PISCO_FETCH_PACKED) {
+        set_error(nullptr, "beam_fetch %d is not PISCO_FETCH_TEXTURE, PISCO_FETCH_CELLS or PISCO_FETCH_PACKED",
+                  fetch);
         return PISCO_EINVAL;
     }
     if (!is_device_ptr(sky) || !is_device_ptr(beam_grids)) {
@@ -226,6 +244,7 @@ extern "C" pisco_status pisco_plan_create(pisco_plan** out, int nside, double ra
     if (precision == PISCO_FP64_PLAIN) p->beam_stride = 3 * nn * sizeof(double);
     else if (mr) p->beam_stride = nc * 4 * sizeof(float4);
     else if (fetch == PISCO_FETCH_CELLS) p->beam_stride = nc * 4 * sizeof(float4);
+    else if (fetch == PISCO_FETCH_PACKED) p->beam_stride = (nc + 1) * 32;  // 32-byte header + cells
     else p->beam_stride = 0;
     const size_t sky_bytes = mr ? (size_t)p->npix * 3 * n_real * 2
                              : precision == PISCO_FP32 ? p->npix * sizeof(float4) : 3 * p->npix * sizeof(double);
@@ -260,6 +279,12 @@ extern "C" pisco_status pisco_plan_create(pisco_plan** out, int nside, double ra
         free_plan(p);
         set_error(nullptr, "plan set-up failed: %s", cudaGetErrorString(e));
         return PISCO_ECUDA;
+    }
+    int bad = -1;
+    if (!packed_range_ok(p, &bad)) {
+        set_error(nullptr, "detector %d: beam slopes outside the packed cells' range; use PISCO_FETCH_CELLS", bad);
+        free_plan(p);
+        return PISCO_EINVAL;
     }
     for (int d = 0; d < n_det; ++d) {
         if (omega_tilde) p->h_omega[d] = omega_tilde[d];
@@ -378,6 +403,8 @@ pisco_status pisco::run(pisco_plan* plan, int mode, int d0, int nd, const int64_
         } else if (plan->precision == PISCO_FP64_PLAIN) e = launch_plain(L, mode, s);
         else if (plan->beam_fetch == PISCO_FETCH_CELLS)
             e = launch_fast_cells(L, mode, plan->tile_samples, plan->pixels_per_thread, s);
+        else if (plan->beam_fetch == PISCO_FETCH_PACKED)
+            e = launch_fast_packed(L, mode, plan->tile_samples, plan->pixels_per_thread, s);
         else e = launch_fast_texture(L, mode, plan->tile_samples, plan->pixels_per_thread, s);
         if (e != cudaSuccess) {
             set_error(plan, "kernel launch failed: %s", cudaGetErrorString(e));
@@ -458,8 +485,8 @@ extern "C" pisco_status pisco_convolve_psb(pisco_plan* plan, int det, int64_t n,
             set_error(plan, "zeta[%d] is not finite", k);
             return PISCO_EINVAL;
         }
-    if (plan->precision != PISCO_FP32 || plan->beam_fetch != PISCO_FETCH_CELLS) {
-        set_error(plan, "pisco_convolve_psb needs an FP32 plan with PISCO_FETCH_CELLS");
+    if (plan->precision != PISCO_FP32 || plan->beam_fetch == PISCO_FETCH_TEXTURE) {
+        set_error(plan, "pisco_convolve_psb needs an FP32 plan with PISCO_FETCH_CELLS or PISCO_FETCH_PACKED");
         return PISCO_EUNSUPPORTED;
     }
     pisco_status st = check_pointing(plan, n, theta, phi, psi);
@@ -610,6 +637,12 @@ extern "C" pisco_status pisco_update_beams(pisco_plan* plan, const float* beam_g
         free(h);
         set_error(plan, "beam update failed: %s", cudaGetErrorString(e));
         return PISCO_ECUDA;
+    }
+    int bad = -1;
+    if (!packed_range_ok(plan, &bad)) {
+        free(h);
+        set_error(plan, "detector %d: beam slopes outside the packed cells' range; use PISCO_FETCH_CELLS", bad);
+        return PISCO_EINVAL;
     }
     for (int d = 0; d < plan->n_det; ++d) {
         const double om = omega_tilde ? omega_tilde[d] : h[d];

@@ -23,8 +23,10 @@
 //  5. the three folded beam maps are interpolated bilinearly at the
 //     orthographic grid coordinates (u, v) = (x, y) (Sec. 4.2), either from
 //     64-byte coefficient cells read through L1/L2 (one 32-byte and one
-//     16-byte load) or from 2 x 2 texel gathers of the node maps through the
-//     texture path (grids of 100s of KB to MB, read at scattered cells);
+//     16-byte load), from 32-byte packed cells (FP32 values, int16 slopes on
+//     a per-cell power-of-two scale; one 32-byte load) or from 2 x 2 texel
+//     gathers of the node maps through the texture path (grids of 100s of KB
+//     to MB, read at scattered cells);
 //  6. the Ludwig-3 angle (Appendix A) enters through
 //        e^{2 i chi} = e^{2 i zeta} (-e1 + i e2)^2 / sin^2(theta_k),
 //        e1 = Z_theta - x (Z_p + m), e2 = Z_phi - y (Z_p + m),
@@ -110,6 +112,10 @@ static __device__ __forceinline__ float4 ld_nc_v4(const float* p) {
     return a;
 }
 
+// Signed 16-bit halves of a packed word, as floats.
+static __device__ __forceinline__ float lo16(unsigned w) { return (float)(int)(short)(w & 0xffffu); }
+static __device__ __forceinline__ float hi16(unsigned w) { return (float)((int)w >> 16); }
+
 // Resident CTAs per SM the register allocation targets, per mode (measured on the
 // single-detector workload, 16-sample tiles): 3 (80 registers, a few spilled to
 // L1) runs the forward and sky-adjoint passes 10 % faster than 2 (128 registers);
@@ -149,6 +155,8 @@ __global__ void __launch_bounds__(NT, fast_min_blocks(MODE)) k_fast(const __grid
         const long long t0 = det.begin + lt * S;
         const int ns = (int)min((long long)S, det.count - lt * S);
         const float* __restrict__ cells = (const float*)det.beam;
+        // packed cells: biased exponent of the unit slope scale, from the 32-byte header
+        const int qbase = FETCH == PISCO_FETCH_PACKED ? __ldg((const int*)det.beam) : 0;
 
         // 1. per-sample constants
         if (tid < S) {
@@ -480,6 +488,23 @@ __global__ void __launch_bounds__(NT, fast_min_blocks(MODE)) k_fast(const __grid
                                 bA = fmaf(fy, fmaf(fx, ka.w, ka.z), fmaf(fx, ka.y, ka.x));
                                 bB = fmaf(fy, fmaf(fx, kb.w, kb.z), fmaf(fx, kb.y, kb.x));
                                 bC = fmaf(fy, fmaf(fx, kc.w, kc.z), fmaf(fx, kc.y, kc.x));
+                            } else if (FETCH == PISCO_FETCH_PACKED) {
+                                const int cell = (int)flv * nc + (int)flu;
+                                if (cell != lastcell[p4]) {
+                                    ld_nc_v8(cells + 8 * (cell + 1), cka[p4], ckb[p4]);  // after the header
+                                    lastcell[p4] = cell;
+                                }
+                                const float4 lo = cka[p4], hi = ckb[p4];
+                                const unsigned w3 = __float_as_uint(lo.w), w4 = __float_as_uint(hi.x);
+                                const unsigned w5 = __float_as_uint(hi.y), w6 = __float_as_uint(hi.z);
+                                const unsigned w7 = __float_as_uint(hi.w);
+                                const unsigned ex = w7 >> 16;
+                                const float sA = __int_as_float((qbase + (int)(ex & 31u)) << 23);
+                                const float sB = __int_as_float((qbase + (int)((ex >> 5) & 31u)) << 23);
+                                const float sC = __int_as_float((qbase + (int)((ex >> 10) & 31u)) << 23);
+                                bA = fmaf(sA, fmaf(fy, fmaf(fx, lo16(w4), hi16(w3)), fx * lo16(w3)), lo.x);
+                                bB = fmaf(sB, fmaf(fy, fmaf(fx, hi16(w5), lo16(w5)), fx * hi16(w4)), lo.y);
+                                bC = fmaf(sC, fmaf(fy, fmaf(fx, lo16(w7), hi16(w6)), fx * lo16(w6)), lo.z);
                             } else {
                                 // texel centres sit at integer + 1/2: (flu + 1, flv + 1) selects
                                 // nodes flu, flu + 1 and flv, flv + 1 exactly
@@ -594,8 +619,8 @@ static cudaError_t launch_s(const LaunchParams& p, int mode, cudaStream_t s) {
     const unsigned grid = (unsigned)min(p.total_tiles, (long long)INT_MAX);
     if (mode == kPsb) {
         // three accumulators per sample: instantiated for beam cells only
-        if constexpr (FETCH == PISCO_FETCH_CELLS) {
-            k_fast<S, NP, PISCO_FETCH_CELLS, kPsb><<<grid, NT, 0, s>>>(p);
+        if constexpr (FETCH != PISCO_FETCH_TEXTURE) {
+            k_fast<S, NP, FETCH, kPsb><<<grid, NT, 0, s>>>(p);
             return cudaGetLastError();
         }
         return cudaErrorInvalidValue;

@@ -134,6 +134,7 @@ inline size_t folded_grad_bytes(int grid_n, int f64) {
 // Launchers (defined in the kernel translation units).
 cudaError_t launch_fast_texture(const LaunchParams& p, int mode, int tile_samples, int np, cudaStream_t s);
 cudaError_t launch_fast_cells(const LaunchParams& p, int mode, int tile_samples, int np, cudaStream_t s);
+cudaError_t launch_fast_packed(const LaunchParams& p, int mode, int tile_samples, int np, cudaStream_t s);
 cudaError_t launch_plain(const LaunchParams& p, int mode, cudaStream_t s);
 cudaError_t launch_mr(const LaunchParams& p, int f16, cudaStream_t s);
 cudaError_t launch_plan_kernels(pisco_plan* plan, const void* sky, int sky_dtype,

@@ -86,6 +86,105 @@ __global__ void k_cells(const float* __restrict__ g, int n, double eps, double z
     cells[4 * cell + 3] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
+// Packed 32-byte cells (PISCO_FETCH_PACKED).  Per cell and folded map m the
+// bilinear form f = c0 + d1 fx + d2 fy + d3 fx fy keeps c0 in FP32 and the three
+// slopes as int16 on a block scale 2^(E - 31 + e_m), E one exponent per detector
+// (from the largest slope of the grid) and e_m in [0, 31] per cell and map, so
+// a slope is off by at most 2^-15 of the largest slope of its cell and map.
+// Layout (eight 32-bit words): c0_A, c0_B, c0_C, (A1 | A2), (A3 | B1), (B2 | B3),
+// (C1 | C2), (C3 | e_A | e_B << 5 | e_C << 10), slope k of map m in 16 bits
+// (low half first).  A 32-byte header precedes the cells: word 0 = E - 31 + 127
+// (the biased exponent of the unit scale), word 1 = the largest |slope| as
+// float bits, word 2 = 1 when E falls outside the normal float range.
+struct Slopes {
+    double c0[3], d[3][3];
+};
+
+__device__ __forceinline__ Slopes cell_slopes(const float* __restrict__ g, int n, long long cell, double eps,
+                                              double c2z, double s2z) {
+    const int nc = n - 1;
+    const int i = (int)(cell % nc), j = (int)(cell / nc);
+    const long long nn = (long long)n * n;
+    const Folded f00 = fold_node(g, nn, (long long)j * n + i, eps, c2z, s2z);
+    const Folded f10 = fold_node(g, nn, (long long)j * n + i + 1, eps, c2z, s2z);
+    const Folded f01 = fold_node(g, nn, (long long)(j + 1) * n + i, eps, c2z, s2z);
+    const Folded f11 = fold_node(g, nn, (long long)(j + 1) * n + i + 1, eps, c2z, s2z);
+    const double v00[3] = {f00.a, f00.b, f00.c}, v10[3] = {f10.a, f10.b, f10.c};
+    const double v01[3] = {f01.a, f01.b, f01.c}, v11[3] = {f11.a, f11.b, f11.c};
+    Slopes r;
+    for (int m = 0; m < 3; ++m) {
+        r.c0[m] = v00[m];
+        r.d[m][0] = v10[m] - v00[m];
+        r.d[m][1] = v01[m] - v00[m];
+        r.d[m][2] = v11[m] - v10[m] - v01[m] + v00[m];
+    }
+    return r;
+}
+
+// Smallest k with |x| <= 2^k (x > 0).
+__device__ __forceinline__ int ceil_log2(double x) {
+    int k;
+    const double f = frexp(x, &k);
+    return f == 0.5 ? k - 1 : k;
+}
+
+__global__ void k_packed_max(const float* __restrict__ g, int n, double eps, double zeta, unsigned* header) {
+    const long long nc = (long long)(n - 1) * (n - 1);
+    const long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (cell >= nc) return;
+    double s2z, c2z;
+    sincos(2.0 * zeta, &s2z, &c2z);
+    const Slopes r = cell_slopes(g, n, cell, eps, c2z, s2z);
+    double mx = 0.0;
+    for (int m = 0; m < 3; ++m)
+        for (int k = 0; k < 3; ++k) mx = fmax(mx, fabs(r.d[m][k]));
+    // non-negative floats order like their bit patterns
+    atomicMax(header + 1, __float_as_uint((float)mx));
+}
+
+__global__ void k_packed_encode(const float* __restrict__ g, int n, double eps, double zeta,
+                                unsigned* __restrict__ header, uint4* __restrict__ out) {
+    const long long nc = (long long)(n - 1) * (n - 1);
+    const long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const float gmax = __uint_as_float(header[1]);
+    // unit scale 2^(E - 31); E such that the largest slope fits 32767 * 2^E
+    const int E = gmax > 0.f ? ceil_log2(1.000001 * (double)gmax / 32767.0) : -90;
+    const bool bad = E - 31 + 127 < 1 || E + 127 > 254;
+    if (cell == 0) {
+        header[0] = (unsigned)(E - 31 + 127);
+        header[2] = bad ? 1u : 0u;
+    }
+    if (cell >= nc || bad) return;
+    double s2z, c2z;
+    sincos(2.0 * zeta, &s2z, &c2z);
+    const Slopes r = cell_slopes(g, n, cell, eps, c2z, s2z);
+    unsigned q[9], ex[3];
+    for (int m = 0; m < 3; ++m) {
+        double mx = 0.0;
+        for (int k = 0; k < 3; ++k) mx = fmax(mx, fabs(r.d[m][k]));
+        int e = mx > 0.0 ? ceil_log2(mx / 32767.0) - (E - 31) : 0;
+        e = e < 0 ? 0 : (e > 31 ? 31 : e);
+        ex[m] = (unsigned)e;
+        const double inv = ldexp(1.0, -(E - 31 + e));
+        for (int k = 0; k < 3; ++k) {
+            double v = rint(r.d[m][k] * inv);
+            v = fmin(32767.0, fmax(-32767.0, v));
+            q[3 * m + k] = (unsigned)((int)v) & 0xffffu;
+        }
+    }
+    uint4 lo, hi;
+    lo.x = __float_as_uint((float)r.c0[0]);
+    lo.y = __float_as_uint((float)r.c0[1]);
+    lo.z = __float_as_uint((float)r.c0[2]);
+    lo.w = q[0] | (q[1] << 16);
+    hi.x = q[2] | (q[3] << 16);
+    hi.y = q[4] | (q[5] << 16);
+    hi.z = q[6] | (q[7] << 16);
+    hi.w = q[8] | ((ex[0] | (ex[1] << 5) | (ex[2] << 10)) << 16);
+    out[2 * (cell + 1)] = lo;  // cell 0 follows the 32-byte header
+    out[2 * (cell + 1) + 1] = hi;
+}
+
 __global__ void k_nodes64(const float* __restrict__ g, int n, double eps, double zeta,
                           double* __restrict__ nodes) {
     const long long nn = (long long)n * n;
@@ -223,9 +322,15 @@ cudaError_t launch_beam_kernels(pisco_plan* plan, const float* grids, cudaStream
         char* dst = plan->d_beam ? (char*)plan->d_beam + (size_t)d * plan->beam_stride : nullptr;
         const pisco_detector& det = plan->h_dets[d];
         if (plan->precision != PISCO_FP64_PLAIN) {
+            const long long nc = (long long)(n - 1) * (n - 1);
             if (plan->beam_fetch == PISCO_FETCH_CELLS) {
-                const long long nc = (long long)(n - 1) * (n - 1);
                 k_cells<<<blocks_for(nc, 256), 256, 0, s>>>(g, n, det.eps, det.zeta, (float4*)dst);
+            } else if (plan->beam_fetch == PISCO_FETCH_PACKED) {
+                cudaError_t e = cudaMemsetAsync(dst, 0, 32, s);
+                if (e != cudaSuccess) return e;
+                k_packed_max<<<blocks_for(nc, 256), 256, 0, s>>>(g, n, det.eps, det.zeta, (unsigned*)dst);
+                k_packed_encode<<<blocks_for(nc, 256), 256, 0, s>>>(g, n, det.eps, det.zeta, (unsigned*)dst,
+                                                                     (uint4*)dst);
             }
         } else {
             k_nodes64<<<blocks_for(nn, 256), 256, 0, s>>>(g, n, det.eps, det.zeta, (double*)dst);
