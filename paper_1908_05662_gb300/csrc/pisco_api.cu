@@ -357,7 +357,7 @@ pisco_status pisco::run(pisco_plan* plan, int mode, int d0, int nd, const int64_
                  const double* theta, const double* phi, const double* psi, void* out, const void* tod_in,
                  int32_t* counts, cudaStream_t s, const PsbAngles* psb) {
     const long long per_tile = plan->precision == PISCO_FP64_PLAIN ? 1
-                               : (plan->precision == PISCO_FP32 ? plan->tile_samples : 16);
+                               : (plan->precision == PISCO_FP32 ? plan->tile_samples : 128);
     for (int c = 0; c < nd; c += kMaxDetPerLaunch) {
         LaunchParams L = base_params(plan);
         L.theta = theta;

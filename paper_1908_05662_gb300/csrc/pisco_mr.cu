@@ -1,25 +1,34 @@
-// Multi-realization convolution on the tensor cores.
+// Multi-realization convolution on the fifth-generation tensor cores (tcgen05).
 //
 // With R sky realizations S_r sharing one scan and one beam, the TOD is a
 // dense contraction (eq. discrete_beam_conv_tensor with the per-pair weights
 // factored out):
 //     d_r(t) = scale * sum_k sum_{m = I,Q,U} W[t][k][m] S_r[k][m],
 //     W[t][k] = (A, (Bq' re + 2 Cu' im2) / sin^2 theta_k, (Cu' re - 2 Bq' im2) / sin^2 theta_k),
-// the pair weights of the FP32 kernel.  One CTA owns 16 consecutive samples
-// (the tile and union disc of the FP32 kernel).  For each super-batch of 64
-// union pixels it
-//   1. streams the realizations, [pixel][I,Q,U][R] in 16-bit, as four slabs of
-//      16 pixels through two shared-memory buffers (rows k = 3 pixel + m,
-//      realizations contiguous) with bulk copies (TMA) completing on one
-//      mbarrier per buffer, each slab issued as soon as its buffer is free;
-//   2. computes the 64 x 16 pair weights in FP32 (zero outside a sample's
-//      disc; four samples per thread, while the first slabs stream) and
-//      splits each into two 16-bit parts, W = W_hi + W_lo with
-//      W_lo the rounded remainder, [sample][k] (the weights keep ~16
-//      significant bits; only the stored realizations are 16-bit);
-//   3. accumulates D[r][t] += sum_k S[k][r] (W_hi[t][k] + W_lo[t][k]) with
-//      m16n8k16 MMAs (realizations = M, samples = N), FP32 accumulators in
-//      registers; warp w owns realizations 32 w .. 32 w + 31.
+// the pair weights of the FP32 kernel.  One CTA owns 128 consecutive samples
+// of one detector, the M dimension of the MMA; the realizations are N (up to
+// 256), so the whole 128 x R accumulator lives in tensor memory (TMEM) for
+// the tile.  The CTA traverses the union of the 128 discs ring by ring (the
+// ring-ordered disc query of the FP32 kernel) and, per batch of 16 union
+// pixels (K = 48: pixel x I, Q, U):
+//   1. copies the realization rows [pixel][I,Q,U][R] (16-bit) with 16-byte
+//      asynchronous copies straight into the B operand's MN-major core-matrix
+//      layout (8 k-rows x 16 bytes per core matrix, no swizzle);
+//   2. computes the 128 x 16 pair weights in FP32 (zero outside a sample's
+//      disc) and splits each into two 16-bit parts, W = W_hi + W_lo
+//      (W_lo the rounded remainder), written in the A operand's K-major
+//      core-matrix layout;
+//   3. one thread issues tcgen05.mma (kind::f16, FP32 accumulate in TMEM) for
+//      W_hi and W_lo over the three K-steps of 16, then tcgen05.commit to the
+//      batch buffer's mbarrier.
+// Operand buffers are double-buffered: the MMAs of one batch run while the
+// threads copy and weigh the next; a buffer is rewritten only after the
+// mbarrier of the MMAs that read it has completed.  At the end of the tile
+// the eight warps read the accumulator rows back with tcgen05.ld (warp w sees
+// TMEM lanes 32 (w % 4) ..; warps w and w + 4 take half the realizations
+// each) and store d[t][r] = scale * D[t][r].  Every wait on an mbarrier is
+// bounded; on a timeout the kernel records error bit 2, drains what it
+// issued and releases its TMEM.
 // Realization stacks are [Npix][3][R] 16-bit (BF16 or FP16), R a multiple of
 // 32 up to 256; the output is FP32 [n][R].
 
@@ -34,16 +43,22 @@ namespace pisco {
 
 namespace {
 
-constexpr int MT = 256;         // threads
-constexpr int MS = 16;          // samples per tile
-constexpr int MRC = 128;        // rings per chunk
-constexpr int KPIX = 16;        // union pixels per batch
-constexpr int KB = 3 * KPIX;    // contraction length per slab
-constexpr int SB_SLABS = 4;     // slabs per super-batch
-constexpr int SBPIX = SB_SLABS * KPIX;  // union pixels per super-batch (weights computed together)
-constexpr int SKY_LD = 264;     // 16-bit elements per staged realization row (256 + 8: ldmatrix rows on distinct banks)
-constexpr int W_LD = KB + 8;    // 16-bit elements per weight row (conflict-free B-fragment loads)
-constexpr int MR_DYN_SMEM = (2 * KB * SKY_LD + 2 * SB_SLABS * MS * W_LD) * 2;
+constexpr int MT = 256;              // threads
+constexpr int MS = 128;              // samples per tile = MMA M
+constexpr int MRC = 32;              // rings per chunk of the union disc
+constexpr int KPIX = 16;             // union pixels per batch
+constexpr int KB = 3 * KPIX;         // contraction length per batch (3 K-steps of 16)
+constexpr int MAXR = 256;            // realizations (MMA N) at most
+// A operand (weights, K-major): core matrix (t / 8, k / 8), 8 rows of 16 bytes
+constexpr int A_LBO = 128;                 // bytes between core matrices adjacent in K
+constexpr int A_SBO = (KB / 8) * 128;      // bytes between core matrices adjacent in M (768)
+constexpr int A_BYTES = MS * KB * 2;       // one 16-bit weight part of a batch (12 KB)
+// B operand (realizations, MN-major): core matrix (k / 8, r / 8), 8 k-rows of 16 bytes
+constexpr int B_SBO = 128;                 // bytes between core matrices adjacent in N
+constexpr int B_BYTES = KB * MAXR * 2;     // a batch's realization rows (24 KB at R = 256)
+// dynamic shared memory: [2 buffers] x (B, A_hi, A_lo)
+constexpr int BUF_BYTES = B_BYTES + 2 * A_BYTES;
+constexpr int MR_DYN_SMEM = 2 * BUF_BYTES + 1024;  // + alignment slack
 
 // x split into a rounded 16-bit part and the rounded remainder.
 __device__ __forceinline__ void split16(float x, int f16, unsigned short& hi, unsigned short& lo) {
@@ -58,38 +73,6 @@ __device__ __forceinline__ void split16(float x, int f16, unsigned short& hi, un
         hi = *reinterpret_cast<const unsigned short*>(&h);
         lo = *reinterpret_cast<const unsigned short*>(&l);
     }
-}
-
-__device__ __forceinline__ void mma16816(float* d, const unsigned* a, unsigned b0, unsigned b1, int f16) {
-    if (f16) {
-        asm volatile(
-            "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-            "{%0,%1,%2,%3};"
-            : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-    } else {
-        asm volatile(
-            "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-            "{%0,%1,%2,%3};"
-            : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-    }
-}
-
-__device__ __forceinline__ void ldsm_x4_trans(unsigned* a, const void* p) {
-    const unsigned addr = (unsigned)__cvta_generic_to_shared(p);
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3])
-                 : "r"(addr));
-}
-
-__device__ __forceinline__ void ldg_cell(const float* p, float4& a, float4& b, float4& c) {
-    asm("ld.global.nc.L1::no_allocate.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-        : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
-        : "l"(p));
-    asm("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
-        : "=f"(c.x), "=f"(c.y), "=f"(c.z), "=f"(c.w)
-        : "l"(p + 8));
 }
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -115,7 +98,41 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
     }
 }
 
-// Pixel data of union pixel f of the current chunk (thread tid of a batch).
+// Shared-memory matrix descriptor of the fifth-generation MMA: start address,
+// leading (K-direction) and stride (M/N-direction) byte offsets between core
+// matrices, descriptor version 1, no swizzle.
+__device__ __forceinline__ unsigned long long smem_desc(unsigned addr, unsigned lbo, unsigned sbo) {
+    return (unsigned long long)((addr >> 4) & 0x3FFFu) | ((unsigned long long)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((unsigned long long)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulate, A and B both BF16 (or
+// both FP16), A K-major, B MN-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__device__ __forceinline__ unsigned instr_desc(int f16, int n, int m) {
+    const unsigned fmt = f16 ? 0u : 1u;
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | (0u << 15) | (1u << 16) | ((unsigned)(n >> 3) << 17) |
+           ((unsigned)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_f16(unsigned dtmem, unsigned long long ad, unsigned long long bd, unsigned idesc,
+                                        unsigned accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(dtmem),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(unsigned long long* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+
+// Pixel data of union pixel f of the current chunk.
 __device__ __forceinline__ void batch_pixel(int b0, int tid, int nr, int total, const int* sPref, const int* sJlo,
                                             const int* sRc, const int* sJref, const float* sDph, const float* sAref,
                                             const int* sFirst, int* bRi, int* bJw, int* bOk, float* bSa, float* bCa,
@@ -145,38 +162,6 @@ __device__ __forceinline__ void batch_pixel(int b0, int tid, int nr, int total, 
     bSa[tid] = sa;
     bCa[tid] = ca;
     bPix[tid] = ok ? (long long)sFirst[ri] + jw : 0;
-}
-
-// Warp 0 copies the realization rows [pixel][I,Q,U][R] of a batch into slab
-// buffer `buf` with bulk copies (TMA) that complete on the buffer's mbarrier:
-// lane 0 arms it with the byte count, lane p < KPIX copies pixel p's 3 rows.
-__device__ __forceinline__ void issue_slab(int lane, const int* ok, const long long* pix,
-                                           const unsigned short* sky16, int nreal, unsigned short* sSky,
-                                           unsigned long long* mbar, int buf) {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    const unsigned row_bytes = (unsigned)nreal * 2u;
-    int nvalid = 0;
-#pragma unroll
-    for (int p = 0; p < KPIX; ++p) nvalid += ok[p];
-    const unsigned bar = smem_u32(mbar + buf);
-    if (lane == 0) {
-        unsigned long long state;
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;"
-                     : "=l"(state)
-                     : "r"(bar), "r"((unsigned)(3 * nvalid) * row_bytes)
-                     : "memory");
-    }
-    __syncwarp();
-    if (lane < KPIX && ok[lane]) {
-        for (int m = 0; m < 3; ++m) {
-            const unsigned short* src = sky16 + (pix[lane] * 3 + m) * nreal;
-            unsigned short* dst = sSky + ((size_t)buf * KB + 3 * lane + m) * SKY_LD;
-            asm volatile(
-                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                ::"r"(smem_u32(dst)), "l"(src), "r"(row_bytes), "r"(bar)
-                : "memory");
-        }
-    }
 }
 
 // In-frame geometry of one (pixel, sample) pair, as in the FP32 kernel: returns
@@ -214,48 +199,67 @@ __device__ __forceinline__ float rcp_approx(float x) {
 }  // namespace
 
 template <int F16>
-__global__ void __launch_bounds__(MT, 2) k_mr(const __grid_constant__ LaunchParams P) {
+__global__ void __launch_bounds__(MT, 1) k_mr(const __grid_constant__ LaunchParams P) {
     __shared__ double sTh[MS], sPh[MS], sPx[MS], sPy[MS], sPz[MS];
     __shared__ float4 sA[MS], sB[MS];
     __shared__ float sBf[MS];
-    __shared__ int sValid[MS], sGs[MS], sGe[MS];
-    __shared__ int sNg, sRlo, sRhi;
+    __shared__ int sValid[MS];
+    __shared__ int sAny, sRlo, sRhi;
     __shared__ double sPhiC;
     __shared__ float2 sPA[MRC * MS];
     __shared__ float sLo[MRC], sHi[MRC];
-    __shared__ int sFlag[MRC], sJlo[MRC], sJref[MRC], sFirst[MRC], sRc[MRC], sCnt[MRC], sPref[MRC + 1], sWarpTot[MRC / 32];
+    __shared__ int sFlag[MRC], sJlo[MRC], sJref[MRC], sFirst[MRC], sRc[MRC], sPref[MRC + 1];
     __shared__ float sAref[MRC], sSr[MRC], sInv[MRC], sDph[MRC];
-    // pixel data of the current super-batch
-    __shared__ int bRi[SBPIX], bJw[SBPIX], bOk[SBPIX];
-    __shared__ long long bPix[SBPIX];
-    __shared__ float bSa[SBPIX], bCa[SBPIX];
+    __shared__ int bRi[KPIX], bJw[KPIX], bOk[KPIX];
+    __shared__ long long bPix[KPIX];
+    __shared__ float bSa[KPIX], bCa[KPIX];
     __shared__ __align__(8) unsigned long long mbar[2];
+    __shared__ unsigned tmem_base;
     __shared__ int failed;
-    extern __shared__ __align__(16) unsigned short mr_dyn[];
-    unsigned short* sSky = mr_dyn;                  // [2][KB][SKY_LD] realization slabs
-    unsigned short* sW = mr_dyn + 2 * KB * SKY_LD;  // [SB_SLABS][MS][W_LD] high parts
-    unsigned short* sWl = sW + SB_SLABS * MS * W_LD;  // [SB_SLABS][MS][W_LD] low parts
+    extern __shared__ unsigned char mr_dyn_raw[];
+    // operand buffers, 1024-byte aligned: buffer b = [B | A_hi | A_lo]
+    unsigned char* dyn = mr_dyn_raw + ((1024u - (smem_u32(mr_dyn_raw) & 1023u)) & 1023u);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned short* __restrict__ sky16 = (const unsigned short*)P.sky;
     const int nreal = P.n_real;
     const int nc = P.grid_n - 1;
     const float gmax = (float)(P.grid_n - 2);
-    const bool mma_warp = warp * 32 < nreal;
+    const int b_lbo = (nreal / 8) * 128;  // B: bytes between core matrices adjacent in K
+    const unsigned ncols = nreal <= 32 ? 32u : (nreal <= 64 ? 64u : (nreal <= 128 ? 128u : 256u));
+    const unsigned idesc = instr_desc(F16, nreal, MS);
 
-    // Both slab buffers start zeroed (a row a batch leaves unwritten then holds
-    // finite stale values, multiplied by zero weights); then the mbarriers.
-    for (int q = tid; q < 2 * KB * SKY_LD / 8; q += MT) ((uint4*)sSky)[q] = make_uint4(0u, 0u, 0u, 0u);
+    // zeroed operand buffers, the two mbarriers, the accumulator columns
+    for (int q = tid; q < 2 * BUF_BYTES / 16; q += MT) ((uint4*)dyn)[q] = make_uint4(0u, 0u, 0u, 0u);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
     if (tid == 0) {
         mbar_init(mbar + 0);
         mbar_init(mbar + 1);
         failed = 0;
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const unsigned tmem = tmem_base;
     unsigned phase[2] = {0u, 0u};
+    bool pend[2] = {false, false};
 
-    for (long long tile = blockIdx.x; tile < P.total_tiles; tile += gridDim.x) {
+    // wait for the MMAs that read buffer b (all threads); false after a timeout
+    auto drain = [&](int b) -> bool {
+        if (!pend[b]) return true;
+        pend[b] = false;
+        const bool ok = mbar_wait(mbar + b, phase[b]);
+        phase[b] ^= 1u;
+        return ok;
+    };
+
+    for (long long tile = blockIdx.x; tile < P.total_tiles && !failed; tile += gridDim.x) {
         int d = 0;
         while (d + 1 < P.ndet && P.det[d + 1].tile_begin <= tile) ++d;
         const DetEntry& det = P.det[d];
@@ -264,6 +268,7 @@ __global__ void __launch_bounds__(MT, 2) k_mr(const __grid_constant__ LaunchPara
         const int ns = (int)min((long long)MS, det.count - lt * MS);
         const float* __restrict__ cells = (const float*)det.beam;
 
+        // 1. per-sample constants (FP64), relative to the first valid sample's longitude
         if (tid < MS) {
             const int i = tid;
             bool ok = i < ns;
@@ -301,306 +306,271 @@ __global__ void __launch_bounds__(MT, 2) k_mr(const __grid_constant__ LaunchPara
         }
         __syncthreads();
         if (tid == 0) {
-            int ng = 0, i = 0;
-            while (i < MS) {
-                if (!sValid[i]) {
-                    ++i;
-                    continue;
+            int first = -1;
+            double tmin = 1e9, tmax = -1e9;
+            for (int i = 0; i < MS; ++i)
+                if (sValid[i]) {
+                    if (first < 0) first = i;
+                    tmin = fmin(tmin, sTh[i]);
+                    tmax = fmax(tmax, sTh[i]);
                 }
-                int j = i + 1;
-                for (; j < MS; ++j) {
-                    if (!sValid[j]) continue;
-                    const double c = sPx[i] * sPx[j] + sPy[i] * sPy[j] + sPz[i] * sPz[j];
-                    double db = sPh[j] - sPh[i];
-                    db -= kTwoPi * rint(db / kTwoPi);
-                    if (c < P.group_cos || fabs(db) > (double)P.group_dphi) break;
-                }
-                sGs[ng] = i;
-                sGe[ng] = j;
-                ++ng;
-                i = j;
-            }
-            sNg = ng;
+            sAny = first >= 0;
+            sPhiC = first >= 0 ? sPh[first] : 0.0;
+            int ra = 0, rb = -1;
+            if (first >= 0) ring_range(tmin, tmax, P.radius, P.nside, &ra, &rb);
+            sRlo = ra;
+            sRhi = rb;
         }
         __syncthreads();
-        const int ngroups = sNg;
+        if (tid < MS && sValid[tid]) {
+            double db = sPh[tid] - sPhiC;
+            db -= kTwoPi * rint(db / kTwoPi);
+            double sb, cb;
+            sincos(0.5 * db, &sb, &cb);
+            sA[tid].x = (float)cb;
+            sA[tid].y = (float)sb;
+            sBf[tid] = (float)db;
+        }
+        __syncthreads();
 
-        // accumulators: [m-tile][n-tile][4], realizations warp*32 + mt*16 + ..., samples nt*8 + ...
-        float acc[2][2][4];
-#pragma unroll
-        for (int a = 0; a < 2; ++a)
-#pragma unroll
-            for (int b = 0; b < 2; ++b)
-#pragma unroll
-                for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
-
-        for (int g = 0; g < ngroups; ++g) {
-            const int gs = sGs[g], ge = sGe[g];
-            if (tid < MS && tid >= gs && tid < ge && sValid[tid]) {
-                double db = sPh[tid] - sPh[gs];
-                db -= kTwoPi * rint(db / kTwoPi);
-                double sb, cb;
-                sincos(0.5 * db, &sb, &cb);
-                sA[tid].x = (float)cb;
-                sA[tid].y = (float)sb;
-                sBf[tid] = (float)db;
-            }
-            if (tid == 0) {
-                sPhiC = sPh[gs];
-                double tmin = 1e9, tmax = -1e9;
-                for (int i = gs; i < ge; ++i)
-                    if (sValid[i]) {
-                        tmin = fmin(tmin, sTh[i]);
-                        tmax = fmax(tmax, sTh[i]);
-                    }
-                int ra, rb;
-                ring_range(tmin, tmax, P.radius, P.nside, &ra, &rb);
-                sRlo = ra;
-                sRhi = rb;
-            }
-            __syncthreads();
-            const int rlo = sRlo, rhi = sRhi;
-            for (int c0 = rlo; c0 <= rhi; c0 += MRC) {
-                const int nr = min(MRC, rhi - c0 + 1);
-                for (int item = tid; item < MRC * MS; item += MT) {
-                    const int ri = item / MS, i = item % MS;
-                    float lo = __int_as_float(0x7f800000), hi = -__int_as_float(0x7f800000);
-                    int full = 0;
+        int batch = 0;  // batches issued in this tile (the first one overwrites the accumulator)
+        const int rlo = sRlo, rhi = sRhi;
+        for (int c0 = rlo; c0 <= rhi && !failed; c0 += MRC) {
+            const int nr = min(MRC, rhi - c0 + 1);
+            // 2. per (ring, sample): sin(dtheta), 1 - cos(dtheta); union of the discs' longitude ranges.
+            //    Thread (ring tid / 8, samples tid % 8 + 8 j).
+            {
+                const int ri = tid >> 3, sub = tid & 7;
+                float lo = __int_as_float(0x7f800000), hi = -__int_as_float(0x7f800000);
+                int full = 0;
+                const bool ring_ok = ri < nr;
+                const RingInfo* R = ring_ok ? &P.rings[c0 + ri] : nullptr;
+#pragma unroll 4
+                for (int j = 0; j < MS / 8; ++j) {
+                    const int i = sub + 8 * j;
                     float2 pa = make_float2(0.f, 1e30f);
-                    if (ri < nr && i >= gs && i < ge && sValid[i]) {
-                        const RingInfo& R = P.rings[c0 + ri];
-                        const float h = (float)(0.5 * (R.theta - sTh[i]));
+                    if (ring_ok && sValid[i]) {
+                        const float h = (float)(0.5 * (R->theta - sTh[i]));
                         float sh, ch;
                         sincosf(h, &sh, &ch);
                         const float av = 2.f * sh * sh;
                         pa = make_float2(2.f * sh * ch, av);
                         if (av <= P.wr_hi) {
-                            const float b2 = 2.f * sB[i].y * R.s_f;
+                            const float b2 = 2.f * sB[i].y * R->s_f;
                             const float tau = (P.wr_hi - av) / b2;
                             if (!(b2 > 0.f) || !(tau < 0.999f)) {
                                 full = 1;
                             } else {
                                 const float hw = 2.f * asinf(sqrtf(fmaxf(tau, 0.f)));
-                                lo = sBf[i] - hw;
-                                hi = sBf[i] + hw;
+                                lo = fminf(lo, sBf[i] - hw);
+                                hi = fmaxf(hi, sBf[i] + hw);
                             }
                         }
                     }
-                    sPA[item] = pa;
-#pragma unroll
-                    for (int off = MS / 2; off > 0; off >>= 1) {
-                        lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, off, MS));
-                        hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, off, MS));
-                        full |= __shfl_xor_sync(0xffffffffu, full, off, MS);
-                    }
-                    if (i == 0 && ri < nr) {
-                        sLo[ri] = lo;
-                        sHi[ri] = hi;
-                        sFlag[ri] = full ? 2 : (lo <= hi ? 1 : 0);
-                    }
+                    sPA[ri * MS + i] = pa;
                 }
-                __syncthreads();
-                int cnt = 0;
-                if (tid < MRC) {
-                    int jlo = 0, jref = 0, first = 0, rc = 1;
-                    float aref = 0.f, sr = 0.f, inv = 0.f, dph = 0.f;
-                    if (tid < nr) {
-                        const RingInfo& R = P.rings[c0 + tid];
-                        const int flag = sFlag[tid];
-                        first = (int)R.first;
-                        rc = R.count;
-                        sr = R.s_f;
-                        inv = R.inv_s2_f;
-                        dph = R.dphi_f;
-                        const double phic = sPhiC;
-                        jref = (int)rint((phic - R.phi0) / R.dphi);
-                        aref = (float)(R.phi0 + (double)jref * R.dphi - phic);
-                        if (flag == 2) {
+#pragma unroll
+                for (int off = 4; off > 0; off >>= 1) {
+                    lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, off, 8));
+                    hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, off, 8));
+                    full |= __shfl_xor_sync(0xffffffffu, full, off, 8);
+                }
+                if (sub == 0) {
+                    sLo[ri] = lo;
+                    sHi[ri] = hi;
+                    sFlag[ri] = ring_ok ? (full ? 2 : (lo <= hi ? 1 : 0)) : 0;
+                }
+            }
+            __syncthreads();
+            // 3. per ring: index range of the union, and its prefix over the chunk (one warp)
+            if (warp == 0) {
+                int cnt = 0, jlo = 0, jref = 0, first = 0, rc = 1;
+                float aref = 0.f, sr = 0.f, inv = 0.f, dph = 0.f;
+                if (lane < nr) {
+                    const RingInfo& R = P.rings[c0 + lane];
+                    const int flag = sFlag[lane];
+                    first = (int)R.first;
+                    rc = R.count;
+                    sr = R.s_f;
+                    inv = R.inv_s2_f;
+                    dph = R.dphi_f;
+                    const double phic = sPhiC;
+                    jref = (int)rint((phic - R.phi0) / R.dphi);
+                    aref = (float)(R.phi0 + (double)jref * R.dphi - phic);
+                    if (flag == 2) {
+                        cnt = R.count;
+                        jlo = jref - R.count / 2;
+                    } else if (flag == 1) {
+                        const double ulo = (phic + (double)sLo[lane] - R.phi0) / R.dphi;
+                        const double uhi = (phic + (double)sHi[lane] - R.phi0) / R.dphi;
+                        const long long a = (long long)floor(ulo) - 1, b = (long long)ceil(uhi) + 1;
+                        if (b - a + 1 >= R.count) {
                             cnt = R.count;
                             jlo = jref - R.count / 2;
-                        } else if (flag == 1) {
-                            const double ulo = (phic + (double)sLo[tid] - R.phi0) / R.dphi;
-                            const double uhi = (phic + (double)sHi[tid] - R.phi0) / R.dphi;
-                            const long long a = (long long)floor(ulo) - 1, b = (long long)ceil(uhi) + 1;
-                            if (b - a + 1 >= R.count) {
-                                cnt = R.count;
-                                jlo = jref - R.count / 2;
-                            } else {
-                                cnt = (int)(b - a + 1);
-                                jlo = (int)a;
-                            }
+                        } else {
+                            cnt = (int)(b - a + 1);
+                            jlo = (int)a;
                         }
                     }
-                    sJlo[tid] = jlo;
-                    sJref[tid] = jref;
-                    sFirst[tid] = first;
-                    sRc[tid] = rc;
-                    sCnt[tid] = cnt;
-                    sAref[tid] = aref;
-                    sSr[tid] = sr;
-                    sInv[tid] = inv;
-                    sDph[tid] = dph;
-                    int v = cnt;
+                }
+                sJlo[lane] = jlo;
+                sJref[lane] = jref;
+                sFirst[lane] = first;
+                sRc[lane] = rc;
+                sAref[lane] = aref;
+                sSr[lane] = sr;
+                sInv[lane] = inv;
+                sDph[lane] = dph;
+                int v = cnt;
 #pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const int y = __shfl_up_sync(0xffffffffu, v, o);
-                        if (lane >= o) v += y;
-                    }
-                    if (lane == 31) sWarpTot[warp] = v;
-                    cnt = v;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, v, o);
+                    if (lane >= o) v += y;
                 }
-                __syncthreads();
-                if (tid < MRC) {
-                    int base = 0;
-                    for (int w = 0; w < warp; ++w) base += sWarpTot[w];
-                    sPref[tid + 1] = base + cnt;
-                    if (tid == 0) sPref[0] = 0;
-                }
-                __syncthreads();
+                sPref[lane + 1] = v;
+                if (lane == 0) sPref[0] = 0;
+            }
+            __syncthreads();
 
-                const int total = sPref[nr];
-                for (int s0 = 0; s0 < total; s0 += SBPIX) {
-                    const int nslab = min(SB_SLABS, (total - s0 + KPIX - 1) / KPIX);
-                    // pixel data of the super-batch (one pixel per thread)
-                    if (tid < SBPIX)
-                        batch_pixel(s0, tid, nr, total, sPref, sJlo, sRc, sJref, sDph, sAref, sFirst, bRi, bJw, bOk,
-                                    bSa, bCa, bPix);
-                    __syncthreads();
-                    // the first two slabs start streaming while the weights are computed
-                    if (warp == 0) {
-                        issue_slab(lane, bOk, bPix, sky16, nreal, sSky, mbar, 0);
-                        if (nslab > 1) issue_slab(lane, bOk + KPIX, bPix + KPIX, sky16, nreal, sSky, mbar, 1);
+            const int total = sPref[nr];
+            for (int f0 = 0; f0 < total && !failed; f0 += KPIX, ++batch) {
+                const int buf = batch & 1;
+                unsigned char* bB = dyn + buf * BUF_BYTES;
+                unsigned char* bAh = bB + B_BYTES;
+                unsigned char* bAl = bAh + A_BYTES;
+                // the MMAs of two batches ago read this buffer
+                if (!drain(buf)) atomicOr(&failed, 1);
+                if (tid < KPIX)
+                    batch_pixel(f0, tid, nr, total, sPref, sJlo, sRc, sJref, sDph, sAref, sFirst, bRi, bJw, bOk, bSa,
+                                bCa, bPix);
+                __syncthreads();
+                if (failed) break;
+                // 4. realization rows into the B operand: 16-byte chunk (k = 3 p + m, r = 8 q .. 8 q + 7)
+                {
+                    const int qn = nreal / 8;
+                    for (int c = tid; c < KB * qn; c += MT) {
+                        const int k = c / qn, q = c % qn;
+                        const int p = k / 3, m = k % 3;
+                        unsigned char* dst = bB + (k >> 3) * b_lbo + q * B_SBO + (k & 7) * 16;
+                        if (bOk[p]) cp_async16(dst, sky16 + (bPix[p] * 3 + m) * (long long)nreal + 8 * q);
+                        else *(uint4*)dst = make_uint4(0u, 0u, 0u, 0u);
                     }
-                    // 2. pair weights: pixel p = tid % 64 for samples tid / 64 + 4 j, j = 0..3.
-                    //    Pass 1 finds the four beam cells and prefetches them into L1 so their
-                    //    latencies overlap; pass 2 recomputes the (cheap) geometry and reads them.
-                    {
-                        const int p = tid & (SBPIX - 1), i0 = tid / SBPIX;
-                        const int q = p / KPIX, pl = p % KPIX;
-                        const bool pok = bOk[p];
-                        const int ri = bRi[p];
-                        const float sr2 = 2.f * sSr[ri], inv = sInv[ri];
-                        const float sa = bSa[p], ca = bCa[p];
-                        int cellv[MS / 4];
-#pragma unroll
-                        for (int j = 0; j < MS / 4; ++j) {
-                            const int i = i0 + 4 * j;
-                            cellv[j] = -1;
-                            if (pok && i >= gs && i < ge) {
-                                PairGeom g;
-                                if (pair_geometry(P, sA[i], sB[i], sPA[ri * MS + i], sa, ca, sr2, gmax, g) &&
-                                    (g.w <= P.wr_lo ||
-                                     exact_in_disc(P.rings, c0 + ri, bJw[p], sPx[i], sPy[i], sPz[i], P.cos_r))) {
-                                    cellv[j] = (int)g.flv * nc + (int)g.flu;
-                                    asm volatile("prefetch.global.L1 [%0];" ::"l"(cells + 16 * cellv[j]));
-                                }
-                            }
+                    asm volatile("cp.async.commit_group;" ::: "memory");
+                }
+                // 5. pair weights, thread (pixel tid % 16, samples tid / 16 + 16 j), into the A operand
+                {
+                    const int p = tid & (KPIX - 1), tb = tid >> 4;
+                    const bool pok = bOk[p];
+                    const int ri = bRi[p];
+                    const float sr2 = 2.f * sSr[ri], inv = sInv[ri];
+                    const float sa = bSa[p], ca = bCa[p];
+#pragma unroll 2
+                    for (int j = 0; j < MS / 16; ++j) {
+                        const int t = tb + 16 * j;
+                        float wI = 0.f, wQ = 0.f, wU = 0.f;
+                        PairGeom g;
+                        if (pok && sValid[t] &&
+                            pair_geometry(P, sA[t], sB[t], sPA[ri * MS + t], sa, ca, sr2, gmax, g) &&
+                            (g.w <= P.wr_lo ||
+                             exact_in_disc(P.rings, c0 + ri, bJw[p], sPx[t], sPy[t], sPz[t], P.cos_r))) {
+                            const float4 B4 = sB[t];
+                            const float* cp = cells + 16 * ((int)g.flv * nc + (int)g.flu);
+                            const float4 ka = __ldg((const float4*)cp), kb = __ldg((const float4*)(cp + 4));
+                            const float4 kc = __ldg((const float4*)(cp + 8));
+                            const float bA = fmaf(g.fy, fmaf(g.fx, ka.w, ka.z), fmaf(g.fx, ka.y, ka.x));
+                            const float bBq = fmaf(g.fy, fmaf(g.fx, kb.w, kb.z), fmaf(g.fx, kb.y, kb.x));
+                            const float bC = fmaf(g.fy, fmaf(g.fx, kc.w, kc.z), fmaf(g.fx, kc.y, kc.x));
+                            const float qr = rcp_approx(2.f - g.w);
+                            const float mp = fmaf(qr, fmaf(g.x, B4.z, g.y * B4.w), B4.x);
+                            const float e1 = fmaf(-g.x, mp, B4.z);
+                            const float e2 = fmaf(-g.y, mp, B4.w);
+                            const float re = fmaf(e1, e1, -e2 * e2);
+                            const float im2 = e1 * e2;
+                            wI = bA;
+                            wQ = fmaf(bBq, re, 2.f * bC * im2) * inv;
+                            wU = fmaf(bC, re, -2.f * bBq * im2) * inv;
                         }
+                        const float wv[3] = {wI, wQ, wU};
 #pragma unroll
-                        for (int j = 0; j < MS / 4; ++j) {
-                            const int i = i0 + 4 * j;
-                            float wI = 0.f, wQ = 0.f, wU = 0.f;
-                            if (cellv[j] >= 0) {
-                                const float4 B4 = sB[i];
-                                PairGeom g;
-                                pair_geometry(P, sA[i], B4, sPA[ri * MS + i], sa, ca, sr2, gmax, g);
-                                const float* cp = cells + 16 * cellv[j];
-                                const float4 ka = __ldg((const float4*)cp), kb = __ldg((const float4*)(cp + 4));
-                                const float4 kc = __ldg((const float4*)(cp + 8));
-                                const float bA = fmaf(g.fy, fmaf(g.fx, ka.w, ka.z), fmaf(g.fx, ka.y, ka.x));
-                                const float bB = fmaf(g.fy, fmaf(g.fx, kb.w, kb.z), fmaf(g.fx, kb.y, kb.x));
-                                const float bC = fmaf(g.fy, fmaf(g.fx, kc.w, kc.z), fmaf(g.fx, kc.y, kc.x));
-                                const float qr = rcp_approx(2.f - g.w);
-                                const float mp = fmaf(qr, fmaf(g.x, B4.z, g.y * B4.w), B4.x);
-                                const float e1 = fmaf(-g.x, mp, B4.z);
-                                const float e2 = fmaf(-g.y, mp, B4.w);
-                                const float re = fmaf(e1, e1, -e2 * e2);
-                                const float im2 = e1 * e2;
-                                wI = bA;
-                                wQ = fmaf(bB, re, 2.f * bC * im2) * inv;
-                                wU = fmaf(bC, re, -2.f * bB * im2) * inv;
-                            }
-                            const int off = (q * MS + i) * W_LD + 3 * pl;
-                            split16(wI, F16, sW[off], sWl[off]);
-                            split16(wQ, F16, sW[off + 1], sWl[off + 1]);
-                            split16(wU, F16, sW[off + 2], sWl[off + 2]);
+                        for (int m = 0; m < 3; ++m) {
+                            const int k = 3 * p + m;
+                            const int off = (t >> 3) * A_SBO + (k >> 3) * A_LBO + (t & 7) * 16 + (k & 7) * 2;
+                            unsigned short h, l;
+                            split16(wv[m], F16, h, l);
+                            *(unsigned short*)(bAh + off) = h;
+                            *(unsigned short*)(bAl + off) = l;
                         }
-                    }
-                    __syncthreads();
-                    // 3. stream the slabs through the two buffers:
-                    //    D[r][t] += sum_k S[k][r] (W_hi[t][k] + W_lo[t][k])
-                    for (int q = 0; q < nslab; ++q) {
-                        const int buf = q & 1;
-                        if (!mbar_wait(mbar + buf, phase[buf])) {
-                            atomicOr(P.err, 2);
-                            failed = 1;
-                        }
-                        phase[buf] ^= 1u;
-                        if (mma_warp && !failed) {
-                            const unsigned short* slab = sSky + buf * KB * SKY_LD;
-                            const unsigned short* wh = sW + q * MS * W_LD;
-                            const unsigned short* wl = sWl + q * MS * W_LD;
-                            const int gq = lane >> 2, cq = lane & 3;
-                            const int mj = lane >> 3, mi = lane & 7;
-#pragma unroll
-                            for (int k0 = 0; k0 < KB; k0 += 16) {
-                                unsigned afr[2][4];
-#pragma unroll
-                                for (int mt = 0; mt < 2; ++mt) {
-                                    const int k = k0 + mi + ((mj >> 1) << 3);
-                                    const int r = warp * 32 + mt * 16 + ((mj & 1) << 3);
-                                    ldsm_x4_trans(afr[mt], slab + k * SKY_LD + r);
-                                }
-#pragma unroll
-                                for (int nt = 0; nt < 2; ++nt) {
-                                    const int off = (nt * 8 + gq) * W_LD + k0 + 2 * cq;
-                                    const unsigned h0 = *(const unsigned*)(wh + off);
-                                    const unsigned h1 = *(const unsigned*)(wh + off + 8);
-                                    const unsigned l0 = *(const unsigned*)(wl + off);
-                                    const unsigned l1 = *(const unsigned*)(wl + off + 8);
-#pragma unroll
-                                    for (int mt = 0; mt < 2; ++mt) {
-                                        mma16816(acc[mt][nt], afr[mt], h0, h1, F16);
-                                        mma16816(acc[mt][nt], afr[mt], l0, l1, F16);
-                                    }
-                                }
-                            }
-                        }
-                        __syncthreads();
-                        if (failed) {
-                            // a copy never arrived: wait (bounded) for the other buffer's copy, then stop
-                            if (q + 1 < nslab) mbar_wait(mbar + (buf ^ 1), phase[buf ^ 1]);
-                            return;
-                        }
-                        // the buffer just read is free: stream slab q + 2 into it
-                        if (q + 2 < nslab && warp == 0)
-                            issue_slab(lane, bOk + (q + 2) * KPIX, bPix + (q + 2) * KPIX, sky16, nreal, sSky, mbar, buf);
                     }
                 }
+                asm volatile("cp.async.wait_group 0;" ::: "memory");
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncthreads();
+                // 6. one thread issues the batch's MMAs: D[t][r] += sum_k (W_hi + W_lo)[t][k] S[k][r]
+                if (tid == 0) {
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+                    for (int ks = 0; ks < KB / 16; ++ks) {
+                        const unsigned long long bd = smem_desc(smem_u32(bB + ks * 2 * b_lbo), b_lbo, B_SBO);
+                        const unsigned long long ah = smem_desc(smem_u32(bAh + ks * 2 * A_LBO), A_LBO, A_SBO);
+                        const unsigned long long al = smem_desc(smem_u32(bAl + ks * 2 * A_LBO), A_LBO, A_SBO);
+                        mma_f16(tmem, ah, bd, idesc, (batch > 0 || ks > 0) ? 1u : 0u);
+                        mma_f16(tmem, al, bd, idesc, 1u);
+                    }
+                    mma_commit(mbar + buf);
+                }
+                pend[buf] = true;
             }
         }
 
-        // output: D[t0 + t][r] = scale * acc, NaN rows for invalid samples
-        if (mma_warp) {
-            const int gq = lane >> 2, cq = lane & 3;
-            float* out = (float*)P.out;
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-                for (int nt = 0; nt < 2; ++nt)
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        const int r = warp * 32 + mt * 16 + gq + ((c >> 1) << 3);
-                        const int t = nt * 8 + 2 * cq + (c & 1);
-                        if (t < ns) {
-                            const float v = sValid[t] ? (float)(det.scale * (double)acc[mt][nt][c])
-                                                      : __int_as_float(0x7fc00000);
-                            out[(t0 + t) * nreal + r] = v;
-                        }
-                    }
+        // 7. epilogue: wait for every MMA of the tile, read D back, d = scale * D (NaN for invalid samples)
+        const bool ok0 = drain(0), ok1 = drain(1);
+        if (!ok0 || !ok1) {
+            atomicOr(P.err, 2);
+            failed = 1;
         }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        __syncthreads();
+        if (failed) break;
+        {
+            const int t = (warp & 3) * 32 + lane;
+            const int half = nreal / 2;
+            const int cbeg = (warp >> 2) * half;
+            float* out = (float*)P.out;
+            const bool valid_row = t < ns;
+            const bool computed = batch > 0;
+            for (int c = cbeg; c < cbeg + half; c += 16) {
+                unsigned r[16];
+                const unsigned addr = tmem + ((unsigned)((warp & 3) * 32) << 16) + (unsigned)c;
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                    "[%16];"
+                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                      "=r"(r[15])
+                    : "r"(addr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (valid_row) {
+                    float v[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        v[j] = !sValid[t] ? __int_as_float(0x7fc00000)
+                                          : (computed ? (float)(det.scale * (double)__uint_as_float(r[j])) : 0.f);
+                    float4* o = (float4*)(out + (t0 + t) * nreal + c);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) o[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+                }
+            }
+        }
+        // the next tile's first MMA overwrites the accumulator: all reads done first
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
     }
+
+    // release the accumulator columns (nothing is left in flight: every commit was waited for,
+    // or the wait timed out and the error flag is set)
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
 }
 
 cudaError_t launch_mr(const LaunchParams& p, int f16, cudaStream_t s) {
