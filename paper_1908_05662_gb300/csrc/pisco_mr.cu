@@ -24,9 +24,9 @@
 // Operand buffers are double-buffered: the MMAs of one batch run while the
 // threads copy and weigh the next; a buffer is rewritten only after the
 // mbarrier of the MMAs that read it has completed.  At the end of the tile
-// the eight warps read the accumulator rows back with tcgen05.ld (warp w sees
-// TMEM lanes 32 (w % 4) ..; warps w and w + 4 take half the realizations
-// each) and store d[t][r] = scale * D[t][r].  Every wait on an mbarrier is
+// the sixteen warps read the accumulator rows back with tcgen05.ld (warp w
+// sees TMEM lanes 32 (w % 4) ..; warps w, w + 4, w + 8, w + 12 take a quarter
+// of the realizations each) and store d[t][r] = scale * D[t][r].  Every wait on an mbarrier is
 // bounded; on a timeout the kernel records error bit 2, drains what it
 // issued and releases its TMEM.
 // Realization stacks are [Npix][3][R] 16-bit (BF16 or FP16), R a multiple of
@@ -43,7 +43,7 @@ namespace pisco {
 
 namespace {
 
-constexpr int MT = 256;              // threads
+constexpr int MT = 512;              // threads
 constexpr int MS = 128;              // samples per tile = MMA M
 constexpr int MRC = 32;              // rings per chunk of the union disc
 constexpr int KPIX = 16;             // union pixels per batch
@@ -338,16 +338,16 @@ __global__ void __launch_bounds__(MT, 1) k_mr(const __grid_constant__ LaunchPara
         for (int c0 = rlo; c0 <= rhi && !failed; c0 += MRC) {
             const int nr = min(MRC, rhi - c0 + 1);
             // 2. per (ring, sample): sin(dtheta), 1 - cos(dtheta); union of the discs' longitude ranges.
-            //    Thread (ring tid / 8, samples tid % 8 + 8 j).
+            //    Thread (ring tid / 16, samples tid % 16 + 16 j).
             {
-                const int ri = tid >> 3, sub = tid & 7;
+                const int ri = tid >> 4, sub = tid & 15;
                 float lo = __int_as_float(0x7f800000), hi = -__int_as_float(0x7f800000);
                 int full = 0;
                 const bool ring_ok = ri < nr;
                 const RingInfo* R = ring_ok ? &P.rings[c0 + ri] : nullptr;
 #pragma unroll 4
-                for (int j = 0; j < MS / 8; ++j) {
-                    const int i = sub + 8 * j;
+                for (int j = 0; j < MS / 16; ++j) {
+                    const int i = sub + 16 * j;
                     float2 pa = make_float2(0.f, 1e30f);
                     if (ring_ok && sValid[i]) {
                         const float h = (float)(0.5 * (R->theta - sTh[i]));
@@ -370,10 +370,10 @@ __global__ void __launch_bounds__(MT, 1) k_mr(const __grid_constant__ LaunchPara
                     sPA[ri * MS + i] = pa;
                 }
 #pragma unroll
-                for (int off = 4; off > 0; off >>= 1) {
-                    lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, off, 8));
-                    hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, off, 8));
-                    full |= __shfl_xor_sync(0xffffffffu, full, off, 8);
+                for (int off = 8; off > 0; off >>= 1) {
+                    lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, off, 16));
+                    hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, off, 16));
+                    full |= __shfl_xor_sync(0xffffffffu, full, off, 16);
                 }
                 if (sub == 0) {
                     sLo[ri] = lo;
@@ -457,16 +457,16 @@ __global__ void __launch_bounds__(MT, 1) k_mr(const __grid_constant__ LaunchPara
                     }
                     asm volatile("cp.async.commit_group;" ::: "memory");
                 }
-                // 5. pair weights, thread (pixel tid % 16, samples tid / 16 + 16 j), into the A operand
+                // 5. pair weights, thread (pixel tid % 16, samples tid / 16 + 32 j), into the A operand
                 {
                     const int p = tid & (KPIX - 1), tb = tid >> 4;
                     const bool pok = bOk[p];
                     const int ri = bRi[p];
                     const float sr2 = 2.f * sSr[ri], inv = sInv[ri];
                     const float sa = bSa[p], ca = bCa[p];
-#pragma unroll 2
-                    for (int j = 0; j < MS / 16; ++j) {
-                        const int t = tb + 16 * j;
+#pragma unroll
+                    for (int j = 0; j < MS / 32; ++j) {
+                        const int t = tb + 32 * j;
                         float wI = 0.f, wQ = 0.f, wU = 0.f;
                         PairGeom g;
                         if (pok && sValid[t] &&
@@ -532,32 +532,30 @@ __global__ void __launch_bounds__(MT, 1) k_mr(const __grid_constant__ LaunchPara
         __syncthreads();
         if (failed) break;
         {
+            // warp w reads TMEM lanes 32 (w % 4) .. (its samples) and a quarter of the realizations
             const int t = (warp & 3) * 32 + lane;
-            const int half = nreal / 2;
+            const int half = nreal / 4;
             const int cbeg = (warp >> 2) * half;
             float* out = (float*)P.out;
             const bool valid_row = t < ns;
             const bool computed = batch > 0;
-            for (int c = cbeg; c < cbeg + half; c += 16) {
-                unsigned r[16];
+            for (int c = cbeg; c < cbeg + half; c += 8) {
+                unsigned r[8];
                 const unsigned addr = tmem + ((unsigned)((warp & 3) * 32) << 16) + (unsigned)c;
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-                    "[%16];"
-                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                      "=r"(r[15])
-                    : "r"(addr));
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                             : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                               "=r"(r[7])
+                             : "r"(addr));
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
                 if (valid_row) {
-                    float v[16];
+                    float v[8];
 #pragma unroll
-                    for (int j = 0; j < 16; ++j)
+                    for (int j = 0; j < 8; ++j)
                         v[j] = !sValid[t] ? __int_as_float(0x7fc00000)
                                           : (computed ? (float)(det.scale * (double)__uint_as_float(r[j])) : 0.f);
                     float4* o = (float4*)(out + (t0 + t) * nreal + c);
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) o[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+                    o[0] = make_float4(v[0], v[1], v[2], v[3]);
+                    o[1] = make_float4(v[4], v[5], v[6], v[7]);
                 }
             }
         }
