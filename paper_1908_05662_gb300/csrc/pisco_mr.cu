@@ -210,9 +210,10 @@ __global__ void __launch_bounds__(MT, 1) k_mr(const __grid_constant__ LaunchPara
     __shared__ float sLo[MRC], sHi[MRC];
     __shared__ int sFlag[MRC], sJlo[MRC], sJref[MRC], sFirst[MRC], sRc[MRC], sPref[MRC + 1];
     __shared__ float sAref[MRC], sSr[MRC], sInv[MRC], sDph[MRC];
-    __shared__ int bRi[KPIX], bJw[KPIX], bOk[KPIX];
-    __shared__ long long bPix[KPIX];
-    __shared__ float bSa[KPIX], bCa[KPIX];
+    // pixel data of the current and the next batch
+    __shared__ int bRi[2][KPIX], bJw[2][KPIX], bOk[2][KPIX];
+    __shared__ long long bPix[2][KPIX];
+    __shared__ float bSa[2][KPIX], bCa[2][KPIX];
     __shared__ __align__(8) unsigned long long mbar[2];
     __shared__ unsigned tmem_base;
     __shared__ int failed;
@@ -433,18 +434,19 @@ __global__ void __launch_bounds__(MT, 1) k_mr(const __grid_constant__ LaunchPara
             __syncthreads();
 
             const int total = sPref[nr];
-            for (int f0 = 0; f0 < total && !failed; f0 += KPIX, ++batch) {
-                const int buf = batch & 1;
+            // the first batch's pixel data; each batch then prepares the next one's
+            if (tid < KPIX && total > 0)
+                batch_pixel(0, tid, nr, total, sPref, sJlo, sRc, sJref, sDph, sAref, sFirst, bRi[0], bJw[0], bOk[0],
+                            bSa[0], bCa[0], bPix[0]);
+            __syncthreads();
+            int fb = 0;  // batch within the chunk
+            for (int f0 = 0; f0 < total && !failed; f0 += KPIX, ++batch, ++fb) {
+                const int buf = batch & 1, pb = fb & 1;
                 unsigned char* bB = dyn + buf * BUF_BYTES;
                 unsigned char* bAh = bB + B_BYTES;
                 unsigned char* bAl = bAh + A_BYTES;
                 // the MMAs of two batches ago read this buffer
                 if (!drain(buf)) atomicOr(&failed, 1);
-                if (tid < KPIX)
-                    batch_pixel(f0, tid, nr, total, sPref, sJlo, sRc, sJref, sDph, sAref, sFirst, bRi, bJw, bOk, bSa,
-                                bCa, bPix);
-                __syncthreads();
-                if (failed) break;
                 // 4. realization rows into the B operand: 16-byte chunk (k = 3 p + m, r = 8 q .. 8 q + 7)
                 {
                     const int qn = nreal / 8;
@@ -452,7 +454,7 @@ __global__ void __launch_bounds__(MT, 1) k_mr(const __grid_constant__ LaunchPara
                         const int k = c / qn, q = c % qn;
                         const int p = k / 3, m = k % 3;
                         unsigned char* dst = bB + (k >> 3) * b_lbo + q * B_SBO + (k & 7) * 16;
-                        if (bOk[p]) cp_async16(dst, sky16 + (bPix[p] * 3 + m) * (long long)nreal + 8 * q);
+                        if (bOk[pb][p]) cp_async16(dst, sky16 + (bPix[pb][p] * 3 + m) * (long long)nreal + 8 * q);
                         else *(uint4*)dst = make_uint4(0u, 0u, 0u, 0u);
                     }
                     asm volatile("cp.async.commit_group;" ::: "memory");
@@ -460,10 +462,10 @@ __global__ void __launch_bounds__(MT, 1) k_mr(const __grid_constant__ LaunchPara
                 // 5. pair weights, thread (pixel tid % 16, samples tid / 16 + 32 j), into the A operand
                 {
                     const int p = tid & (KPIX - 1), tb = tid >> 4;
-                    const bool pok = bOk[p];
-                    const int ri = bRi[p];
+                    const bool pok = bOk[pb][p];
+                    const int ri = bRi[pb][p];
                     const float sr2 = 2.f * sSr[ri], inv = sInv[ri];
-                    const float sa = bSa[p], ca = bCa[p];
+                    const float sa = bSa[pb][p], ca = bCa[pb][p];
 #pragma unroll
                     for (int j = 0; j < MS / 32; ++j) {
                         const int t = tb + 32 * j;
@@ -472,7 +474,7 @@ __global__ void __launch_bounds__(MT, 1) k_mr(const __grid_constant__ LaunchPara
                         if (pok && sValid[t] &&
                             pair_geometry(P, sA[t], sB[t], sPA[ri * MS + t], sa, ca, sr2, gmax, g) &&
                             (g.w <= P.wr_lo ||
-                             exact_in_disc(P.rings, c0 + ri, bJw[p], sPx[t], sPy[t], sPz[t], P.cos_r))) {
+                             exact_in_disc(P.rings, c0 + ri, bJw[pb][p], sPx[t], sPy[t], sPz[t], P.cos_r))) {
                             const float4 B4 = sB[t];
                             const float* cp = cells + 16 * ((int)g.flv * nc + (int)g.flu);
                             const float4 ka = __ldg((const float4*)cp), kb = __ldg((const float4*)(cp + 4));
@@ -502,9 +504,13 @@ __global__ void __launch_bounds__(MT, 1) k_mr(const __grid_constant__ LaunchPara
                         }
                     }
                 }
+                if (tid < KPIX && f0 + KPIX < total)
+                    batch_pixel(f0 + KPIX, tid, nr, total, sPref, sJlo, sRc, sJref, sDph, sAref, sFirst, bRi[pb ^ 1],
+                                bJw[pb ^ 1], bOk[pb ^ 1], bSa[pb ^ 1], bCa[pb ^ 1], bPix[pb ^ 1]);
                 asm volatile("cp.async.wait_group 0;" ::: "memory");
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 __syncthreads();
+                if (failed) break;
                 // 6. one thread issues the batch's MMAs: D[t][r] += sum_k (W_hi + W_lo)[t][k] S[k][r]
                 if (tid == 0) {
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");

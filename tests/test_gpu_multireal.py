@@ -63,7 +63,7 @@ def _oracle_mr(nside, radius, stack64, grids, det, theta, phi, psi):
 
 @pytest.mark.parametrize("precision,dtype,bound", [(pisco.PISCO_BF16_MR, torch.bfloat16, 1e-5),
                                                    (pisco.PISCO_FP16_MR, torch.float16, 2e-6)])
-@pytest.mark.parametrize("n_real", [64, 256])
+@pytest.mark.parametrize("n_real", [64, 96, 160, 256])
 def test_multirealization_matches_oracle_per_realization(precision, dtype, bound, n_real):
     nside, r = 32, math.radians(8.0)
     stack, stack64 = _stack(nside, n_real, dtype, 100)
