@@ -289,6 +289,19 @@ pisco_status pisco_beam_grid_adjoint(pisco_plan* plan, int det, int64_t n,
                                      const void* tod, void* grad_grids, int accumulate, void* stream);
 
 /*
+ * pisco_adjoint_sky_beam -- pisco_adjoint and pisco_beam_grid_adjoint in one
+ * traversal of the discs (the two transposes of the same linear map share
+ * every pair's geometry and beam value): maps (+)= A_S^T tod and
+ * grad_grids (+)= A_G^T tod, with the layouts, the accumulate flag and the
+ * scratch of those two calls.  FP32 plans only (PISCO_EUNSUPPORTED
+ * otherwise); tod, maps and grad_grids float32.
+ */
+pisco_status pisco_adjoint_sky_beam(pisco_plan* plan, int det, int64_t n,
+                                    const double* theta, const double* phi, const double* psi,
+                                    const void* tod, void* maps, void* grad_grids, int accumulate,
+                                    void* stream);
+
+/*
  * pisco_beam_grid_adjoint_static -- pisco_beam_grid_adjoint that allocates
  * nothing.  The paper has no counterpart: this entry point exists for
  * callers that may not allocate device memory when they call (a real-time

@@ -4,7 +4,9 @@
 returns the TOD of one detector (pisco_convolve).  Its backward pass runs
 the library's transposes: pisco_adjoint for the sky (TOD -> I, Q, U maps) and
 pisco_beam_grid_adjoint + pisco_omega_adjoint for the six beam grids (the
-Omega~ term only when Omega~ is computed from B_TT).  Gradients with respect
+Omega~ term only when Omega~ is computed from B_TT); when both gradients are
+wanted from an FP32 plan, pisco_adjoint_sky_beam runs the two transposes in
+one traversal.  Gradients with respect
 to beam parameters (FWHM, ellipticity, cross-polar leakage) follow by
 building ``beam_grids`` from them with ``beams.gaussian_beam_grids``.
 """
@@ -34,10 +36,15 @@ class PiscoConvolve(torch.autograd.Function):
         plan = ctx.plan
         g = grad_tod.contiguous().to(plan.out_dtype)
         grad_sky = grad_beam = None
-        if ctx.needs_input_grad[0]:
-            grad_sky = plan.adjoint(theta, phi, psi, g).to(ctx.sky_dtype)
-        if ctx.needs_input_grad[1]:
-            gb = plan.beam_grid_adjoint(theta, phi, psi, g)
+        both = ctx.needs_input_grad[0] and ctx.needs_input_grad[1]
+        if both and plan.precision == pisco.PISCO_FP32:
+            maps, gb = plan.adjoint_sky_beam(theta, phi, psi, g)  # one traversal for both transposes
+            grad_sky = maps.to(ctx.sky_dtype)
+        else:
+            if ctx.needs_input_grad[0]:
+                grad_sky = plan.adjoint(theta, phi, psi, g).to(ctx.sky_dtype)
+            gb = plan.beam_grid_adjoint(theta, phi, psi, g) if ctx.needs_input_grad[1] else None
+        if gb is not None:
             if not ctx.omega_given:
                 plan.omega_adjoint(tod, g, gb)
             grad_beam = gb.to(ctx.beam_dtype)

@@ -355,7 +355,7 @@ pisco_status pisco::check_pointing(pisco_plan* plan, int64_t n, const double* a,
 
 pisco_status pisco::run(pisco_plan* plan, int mode, int d0, int nd, const int64_t* begin, const int64_t* count,
                  const double* theta, const double* phi, const double* psi, void* out, const void* tod_in,
-                 int32_t* counts, cudaStream_t s, const PsbAngles* psb) {
+                 int32_t* counts, cudaStream_t s, const PsbAngles* psb, void* out2) {
     const long long per_tile = plan->precision == PISCO_FP64_PLAIN ? 1
                                : (plan->precision == PISCO_FP32 ? plan->tile_samples : 128);
     for (int c = 0; c < nd; c += kMaxDetPerLaunch) {
@@ -366,6 +366,7 @@ pisco_status pisco::run(pisco_plan* plan, int mode, int d0, int nd, const int64_
         L.out = out;
         L.tod_in = tod_in;
         L.counts = counts;
+        L.out2 = out2;
         const int m = nd - c < kMaxDetPerLaunch ? nd - c : kMaxDetPerLaunch;
         long long tiles = 0;
         int k = 0;
@@ -684,6 +685,41 @@ extern "C" pisco_status pisco_beam_grid_adjoint(pisco_plan* plan, int det, int64
     }
     PISCO_CUDA(plan, launch_unfold_grid(plan->d_gscratch, plan->grid_n, plan->h_dets[det].eps,
                                         plan->h_dets[det].zeta, grad_grids, accumulate, f64, s));
+    return PISCO_OK;
+}
+
+extern "C" pisco_status pisco_adjoint_sky_beam(pisco_plan* plan, int det, int64_t n, const double* theta,
+                                               const double* phi, const double* psi, const void* tod, void* maps,
+                                               void* grad_grids, int accumulate, void* stream) {
+    if (!plan) return PISCO_EINVAL;
+    if (det < 0 || det >= plan->n_det) {
+        set_error(plan, "detector %d outside [0, %d)", det, plan->n_det);
+        return PISCO_EINVAL;
+    }
+    if (plan->precision != PISCO_FP32) {
+        set_error(plan, "pisco_adjoint_sky_beam needs an FP32 plan; call pisco_adjoint and "
+                        "pisco_beam_grid_adjoint on plain plans");
+        return PISCO_EUNSUPPORTED;
+    }
+    pisco_status st = check_pointing(plan, n, theta, phi, psi);
+    if (st != PISCO_OK) return st;
+    if (!is_device_ptr(maps) || !is_device_ptr(grad_grids) || (n > 0 && !is_device_ptr(tod))) {
+        set_error(plan, "tod, maps and grad_grids must be device pointers");
+        return PISCO_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t bytes = folded_grad_bytes(plan->grid_n, 0);
+    if (!plan->d_gscratch) PISCO_CUDA(plan, cudaMalloc(&plan->d_gscratch, bytes));
+    PISCO_CUDA(plan, cudaMemsetAsync(plan->d_gscratch, 0, bytes, s));
+    if (!accumulate) PISCO_CUDA(plan, cudaMemsetAsync(maps, 0, 3 * (size_t)plan->npix * sizeof(float), s));
+    if (n > 0) {
+        const int64_t begin = 0, count = n;
+        st = run(plan, kBoth, det, 1, &begin, &count, theta, phi, psi, maps, tod, nullptr, s, nullptr,
+                 plan->d_gscratch);
+        if (st != PISCO_OK) return st;
+    }
+    PISCO_CUDA(plan, launch_unfold_grid(plan->d_gscratch, plan->grid_n, plan->h_dets[det].eps,
+                                        plan->h_dets[det].zeta, grad_grids, accumulate, 0, s));
     return PISCO_OK;
 }
 

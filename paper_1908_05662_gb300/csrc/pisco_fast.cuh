@@ -37,11 +37,11 @@
 //     e^{2 i zeta} is folded into the beam maps at plan time;
 //  7. per-sample FP32 partial sums: warp shuffles, then FP64 across warps.
 //
-// The same traversal serves three transposes: the sky adjoint (atomic adds of
+// The same traversal serves the transposes: the sky adjoint (atomic adds of
 // each pixel's I, Q, U weights summed over the group's samples), the
-// beam-grid adjoint (atomic adds into the folded node gradient, accumulated
-// per cell in registers while consecutive samples stay in one cell) and the
-// disc count.
+// beam-grid adjoint (vector reductions into the folded node gradient,
+// accumulated per cell in registers while consecutive samples stay in one
+// cell), both in one pass (they share the geometry), and the disc count.
 //
 // A thread takes NP consecutive pixels of a ring: their sky values are loaded
 // once per group and reused for all S samples, and each per-sample value read
@@ -146,6 +146,8 @@ __global__ void __launch_bounds__(NT, fast_min_blocks(MODE)) k_fast(const __grid
     const float4* __restrict__ sky = (const float4*)P.sky;
     const int nc = P.grid_n - 1;
     const float gmax = (float)(P.grid_n - 2);
+    // beam-grid transpose target: the output, or the second output when both transposes run
+    float* const gout = (float*)(MODE == kBoth ? P.out2 : P.out);
 
     for (long long tile = blockIdx.x; tile < P.total_tiles; tile += gridDim.x) {
         int d = 0;
@@ -184,7 +186,7 @@ __global__ void __launch_bounds__(NT, fast_min_blocks(MODE)) k_fast(const __grid
                 a.z = (float)cs;
                 a.w = (float)ss;
                 b = make_float4((float)ct, (float)st, (float)(-cs * st), (float)(ss * st));
-                if (MODE == kAdjoint || MODE == kGrid)
+                if (MODE == kAdjoint || MODE == kGrid || MODE == kBoth)
                     sY[i] = (float)((double)((const float*)P.tod_in)[t0 + i] * det.scale);
             }
             sTh[i] = th;
@@ -447,10 +449,10 @@ __global__ void __launch_bounds__(NT, fast_min_blocks(MODE)) k_fast(const __grid
                             const float flv = fminf(fmaxf(floorf(fv), 0.f), gmax);
                             const float fx = fmaf(x, P.invh_f, P.cg_f - flu);
                             const float fy = fmaf(y, P.invh_f, P.cg_f - flv);
-                            if (MODE == kGrid) {
+                            if (MODE == kGrid || MODE == kBoth) {
                                 const int cell = (int)flv * nc + (int)flu;
                                 if (cell != gcell[p4]) {
-                                    if (gcell[p4] >= 0) flush_grid((float*)P.out, gcell[p4], nc, P.grid_n, gw[p4]);
+                                    if (gcell[p4] >= 0) flush_grid(gout, gcell[p4], nc, P.grid_n, gw[p4]);
                                     gcell[p4] = cell;
                                 }
                                 const float q = rcp_approx(2.f - w);
@@ -472,7 +474,7 @@ __global__ void __launch_bounds__(NT, fast_min_blocks(MODE)) k_fast(const __grid
                                     gw[p4][4 + k] = fmaf(cB, wt[k], gw[p4][4 + k]);
                                     gw[p4][8 + k] = fmaf(cC, wt[k], gw[p4][8 + k]);
                                 }
-                                continue;
+                                if (MODE == kGrid) continue;
                             }
                             float bA, bB, bC;
                             if (FETCH == PISCO_FETCH_CELLS) {
@@ -537,12 +539,12 @@ __global__ void __launch_bounds__(NT, fast_min_blocks(MODE)) k_fast(const __grid
                             }
                         }
                     }
-                    if (MODE == kGrid) {
+                    if (MODE == kGrid || MODE == kBoth) {
 #pragma unroll
                         for (int p4 = 0; p4 < NP; ++p4)
-                            if (gcell[p4] >= 0) flush_grid((float*)P.out, gcell[p4], nc, P.grid_n, gw[p4]);
+                            if (gcell[p4] >= 0) flush_grid(gout, gcell[p4], nc, P.grid_n, gw[p4]);
                     }
-                    if (MODE == kAdjoint) {
+                    if (MODE == kAdjoint || MODE == kBoth) {
                         float* maps = (float*)P.out;
 #pragma unroll
                         for (int p4 = 0; p4 < NP; ++p4) {
@@ -629,6 +631,7 @@ static cudaError_t launch_s(const LaunchParams& p, int mode, cudaStream_t s) {
         case kForward: k_fast<S, NP, FETCH, kForward><<<grid, NT, 0, s>>>(p); break;
         case kAdjoint: k_fast<S, NP, FETCH, kAdjoint><<<grid, NT, 0, s>>>(p); break;
         case kGrid: k_fast<S, NP, FETCH, kGrid><<<grid, NT, 0, s>>>(p); break;
+        case kBoth: k_fast<S, NP, FETCH, kBoth><<<grid, NT, 0, s>>>(p); break;
         default: k_fast<S, NP, FETCH, kCount><<<grid, NT, 0, s>>>(p); break;
     }
     return cudaGetLastError();

@@ -39,7 +39,7 @@ struct DetEntry {
 
 constexpr int kMaxDetPerLaunch = 64;
 
-enum Mode { kForward = 0, kAdjoint = 1, kCount = 2, kGrid = 3, kPsb = 4 };
+enum Mode { kForward = 0, kAdjoint = 1, kCount = 2, kGrid = 3, kPsb = 4, kBoth = 5 };
 
 constexpr int kMaxPsb = 8;  // polarisation angles per shared-geometry pass
 
@@ -64,6 +64,7 @@ struct LaunchParams {
     const void* tod_in;    // adjoint input
     int32_t* counts;       // count mode output
     int* err;
+    void* out2;            // sky and beam-grid transposes in one pass: the folded beam-grid gradient
     int n_real;            // multi-realization plans: realizations per pixel
     int n_zeta;            // shared-geometry pass: number of polarisation angles
     long long out_stride;  // shared-geometry pass: elements between the TODs of two angles
@@ -123,7 +124,7 @@ pisco_status check_pointing(pisco_plan* plan, int64_t n, const double* a, const 
 // Launch one path over detectors [d0, d0 + nd) with per-detector sample ranges.
 pisco_status run(pisco_plan* plan, int mode, int d0, int nd, const int64_t* begin, const int64_t* count,
                  const double* theta, const double* phi, const double* psi, void* out, const void* tod_in,
-                 int32_t* counts, cudaStream_t s, const PsbAngles* psb = nullptr);
+                 int32_t* counts, cudaStream_t s, const PsbAngles* psb = nullptr, void* out2 = nullptr);
 
 // Bytes of the folded beam-grid gradient scratch: FP32 plans interleave the three
 // folded maps per node with a pad ([N][N][4] floats), the plain path keeps [3][N][N] doubles.

@@ -28,7 +28,7 @@ EXPORTS = ("pisco_plan_create", "pisco_plan_destroy", "pisco_last_error", "pisco
            "pisco_convolve_host", "pisco_sync_status", "pisco_beam_grid_adjoint", "pisco_omega_adjoint",
            "pisco_update_beams", "pisco_beam_grid_adjoint_static", "pisco_convolve_psb",
            "pisco_beam_grids_from_healpix", "pisco_ang2pix", "pisco_map_accumulate", "pisco_map_solve",
-           "pisco_plan_autotune")
+           "pisco_plan_autotune", "pisco_adjoint_sky_beam")
 
 
 class PiscoError(RuntimeError):
@@ -81,6 +81,7 @@ def load_library(path=LIB_PATH):
         "pisco_map_accumulate": (c_int, [c_int, i64, vp, vp, vp, ctypes.POINTER(pisco_detector), vp, c_int, vp,
                                          c_int, vp]),
         "pisco_map_solve": (c_int, [c_int, vp, dbl, vp, vp]),
+        "pisco_adjoint_sky_beam": (c_int, [vp, c_int, i64, vp, vp, vp, vp, vp, vp, c_int, vp]),
         "pisco_plan_autotune": (c_int, [vp, c_int, i64, vp, vp, vp, vp, c_int, ctypes.POINTER(c_int),
                                         ctypes.POINTER(c_int), ctypes.POINTER(ctypes.c_float), vp]),
     }
@@ -257,6 +258,14 @@ def pisco_adjoint(plan, det, theta, phi, psi, tod, maps, accumulate=False):
     return maps
 
 
+def pisco_adjoint_sky_beam(plan, det, theta, phi, psi, tod, maps, grad_grids, accumulate=False):
+    n = theta.numel()
+    _check(load_library().pisco_adjoint_sky_beam(plan, det, n, _ptr(_f64(theta)), _ptr(_f64(phi)),
+                                                 _ptr(_f64(psi)), _ptr(tod), _ptr(maps), _ptr(grad_grids),
+                                                 int(bool(accumulate)), _stream()), plan)
+    return maps, grad_grids
+
+
 def pisco_disc_count(plan, theta, phi, counts):
     n = theta.numel()
     _check(load_library().pisco_disc_count(plan, n, _ptr(_f64(theta)), _ptr(_f64(phi)), _ptr(counts),
@@ -361,6 +370,14 @@ class Plan:
         if grad is None:
             grad = torch.empty(6, self.grid_n, self.grid_n, dtype=self.out_dtype, device=theta.device)
         return pisco_beam_grid_adjoint(self.handle, det, theta, phi, psi, tod, grad, accumulate)
+
+    def adjoint_sky_beam(self, theta, phi, psi, tod, det=0, maps=None, grad=None, accumulate=False):
+        """Both transposes in one pass (FP32 plans): (maps (3, Npix), grad (6, N, N))."""
+        if maps is None:
+            maps = torch.empty(3, 12 * self.nside ** 2, dtype=self.out_dtype, device=theta.device)
+        if grad is None:
+            grad = torch.empty(6, self.grid_n, self.grid_n, dtype=self.out_dtype, device=theta.device)
+        return pisco_adjoint_sky_beam(self.handle, det, theta, phi, psi, tod, maps, grad, accumulate)
 
     def omega_adjoint(self, tod, tod_grad, grad, det=0):
         return pisco_omega_adjoint(self.handle, det, tod, tod_grad, grad)

@@ -153,3 +153,37 @@ def test_update_beams_equals_new_plan():
                 a.update_beams(g2)
                 assert a.omega() == b.omega()
                 torch.testing.assert_close(a.convolve(th, ph, ps), b.convolve(th, ph, ps), rtol=0, atol=0)
+
+
+def test_fused_sky_and_beam_transposes_match_the_separate_ones_and_the_oracle():
+    """pisco_adjoint_sky_beam runs both transposes in one traversal: the same sums as
+    pisco_adjoint and pisco_beam_grid_adjoint (atomic-add order aside) and the oracle's."""
+    nside, r, n = 16, math.radians(15.0), 31
+    grids = sy.random_beam_maps(n, 77)
+    det = (0.6, 0.07, 1.2)
+    sky = sy.white_sky(nside, 8).numpy()
+    th, ph, ps = sy.raster_scan(150, center=(1.2, 2.5), half_size=math.radians(5.0), rows=6)
+    y = np.random.default_rng(12).standard_normal(len(th))
+    omega = ob.omega_tilde(grids[0].astype(np.float64), r)
+    ref_maps = oc.adjoint(nside, r, grids.astype(np.float64), det, omega, th, ph, ps, y)
+    ref_grid = oc.beam_grid_adjoint(nside, r, sky, grids.astype(np.float64), det, omega, th, ph, ps, y)
+    yt = _t(y, torch.float32)
+    with pisco.Plan(nside, r, _t(sky), [det], torch.as_tensor(grids, device=DEV)[None]) as plan:
+        maps, grad = plan.adjoint_sky_beam(_t(th), _t(ph), _t(ps), yt)
+        maps1 = plan.adjoint(_t(th), _t(ph), _t(ps), yt)
+        grad1 = plan.beam_grid_adjoint(_t(th), _t(ph), _t(ps), yt)
+        maps2, grad2 = plan.adjoint_sky_beam(_t(th), _t(ph), _t(ps), yt, maps=maps.clone(), grad=grad.clone(),
+                                             accumulate=True)
+        plan.sync_status()
+    m, g = maps.double().cpu().numpy(), grad.double().cpu().numpy()
+    np.testing.assert_allclose(m, maps1.double().cpu().numpy(), rtol=0, atol=1e-6 * np.max(np.abs(ref_maps)))
+    np.testing.assert_allclose(g, grad1.double().cpu().numpy(), rtol=0, atol=1e-6 * np.max(np.abs(ref_grid)))
+    np.testing.assert_allclose(m, ref_maps, rtol=0, atol=2e-5 * np.max(np.abs(ref_maps)))
+    np.testing.assert_allclose(g, ref_grid, rtol=0, atol=2e-5 * np.max(np.abs(ref_grid)))
+    np.testing.assert_allclose(maps2.double().cpu().numpy(), 2 * m, rtol=0, atol=2e-6 * np.max(np.abs(ref_maps)))
+    np.testing.assert_allclose(grad2.double().cpu().numpy(), 2 * g, rtol=0, atol=2e-6 * np.max(np.abs(ref_grid)))
+    with pisco.Plan(nside, r, _t(sky), [det], torch.as_tensor(grids, device=DEV)[None],
+                    precision=pisco.PISCO_FP64_PLAIN) as plain:
+        with pytest.raises(pisco.PiscoError) as e:
+            plain.adjoint_sky_beam(_t(th), _t(ph), _t(ps), _t(y))
+        assert e.value.status == pisco.PISCO_EUNSUPPORTED
