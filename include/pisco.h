@@ -280,8 +280,9 @@ pisco_status pisco_adjoint(pisco_plan* plan, int det, int64_t n,
  *   grad_grids  device [6][grid_n][grid_n] of the same type, maps ordered as
  *               beam_grids; overwritten unless accumulate != 0.
  * Uses a plan-owned scratch buffer (allocated on the first call) of
- * 4 grid_n^2 floats (FP32 plans, node-interleaved) or 3 grid_n^2 doubles
- * (plain plans), and atomic adds (the last bits vary from run to run).  The
+ * 12 (grid_n - 1)^2 floats (FP32 plans: per cell, the gradients of the three
+ * folded maps' bilinear coefficients) or 3 grid_n^2 doubles (plain plans),
+ * and atomic adds (the last bits vary from run to run).  The
  * dependence of Omega~ on B_TT is added by pisco_omega_adjoint.
  */
 pisco_status pisco_beam_grid_adjoint(pisco_plan* plan, int det, int64_t n,

@@ -355,7 +355,7 @@ pisco_status pisco::check_pointing(pisco_plan* plan, int64_t n, const double* a,
 
 pisco_status pisco::run(pisco_plan* plan, int mode, int d0, int nd, const int64_t* begin, const int64_t* count,
                  const double* theta, const double* phi, const double* psi, void* out, const void* tod_in,
-                 int32_t* counts, cudaStream_t s, const PsbAngles* psb, void* out2) {
+                 int32_t* counts, cudaStream_t s, const PsbAngles* psb, void* out2, int grid_coef) {
     const long long per_tile = plan->precision == PISCO_FP64_PLAIN ? 1
                                : (plan->precision == PISCO_FP32 ? plan->tile_samples : 128);
     for (int c = 0; c < nd; c += kMaxDetPerLaunch) {
@@ -367,6 +367,7 @@ pisco_status pisco::run(pisco_plan* plan, int mode, int d0, int nd, const int64_
         L.tod_in = tod_in;
         L.counts = counts;
         L.out2 = out2;
+        L.grid_coef = grid_coef;
         const int m = nd - c < kMaxDetPerLaunch ? nd - c : kMaxDetPerLaunch;
         long long tiles = 0;
         int k = 0;
@@ -659,6 +660,14 @@ extern "C" pisco_status pisco_update_beams(pisco_plan* plan, const float* beam_g
     return PISCO_OK;
 }
 
+// Bytes of a plan's folded beam-grid gradient scratch: per cell coefficient for FP32
+// plans, per node for the plain path.
+static size_t plan_grad_scratch_bytes(const pisco_plan* plan) {
+    if (plan->precision == PISCO_FP64_PLAIN) return folded_grad_bytes(plan->grid_n, 1);
+    const size_t a = folded_coef_grad_bytes(plan->grid_n), b = folded_grad_bytes(plan->grid_n, 0);
+    return a > b ? a : b;
+}
+
 extern "C" pisco_status pisco_beam_grid_adjoint(pisco_plan* plan, int det, int64_t n, const double* theta,
                                                 const double* phi, const double* psi, const void* tod,
                                                 void* grad_grids, int accumulate, void* stream) {
@@ -675,16 +684,23 @@ extern "C" pisco_status pisco_beam_grid_adjoint(pisco_plan* plan, int det, int64
     }
     cudaStream_t s = (cudaStream_t)stream;
     const int f64 = plan->precision == PISCO_FP64_PLAIN;
-    const size_t bytes = folded_grad_bytes(plan->grid_n, f64);
+    // FP32 plans accumulate per cell coefficient, the plain path per node
+    const size_t bytes = plan_grad_scratch_bytes(plan);
     if (!plan->d_gscratch) PISCO_CUDA(plan, cudaMalloc(&plan->d_gscratch, bytes));
     PISCO_CUDA(plan, cudaMemsetAsync(plan->d_gscratch, 0, bytes, s));
     if (n > 0) {
         const int64_t begin = 0, count = n;
-        st = run(plan, kGrid, det, 1, &begin, &count, theta, phi, psi, plan->d_gscratch, tod, nullptr, s);
+        st = run(plan, kGrid, det, 1, &begin, &count, theta, phi, psi, plan->d_gscratch, tod, nullptr, s, nullptr,
+                 nullptr, f64 ? 0 : 1);
         if (st != PISCO_OK) return st;
     }
-    PISCO_CUDA(plan, launch_unfold_grid(plan->d_gscratch, plan->grid_n, plan->h_dets[det].eps,
-                                        plan->h_dets[det].zeta, grad_grids, accumulate, f64, s));
+    if (f64)
+        PISCO_CUDA(plan, launch_unfold_grid(plan->d_gscratch, plan->grid_n, plan->h_dets[det].eps,
+                                            plan->h_dets[det].zeta, grad_grids, accumulate, 1, s));
+    else
+        PISCO_CUDA(plan, launch_unfold_coef_grid((const float*)plan->d_gscratch, plan->grid_n,
+                                                 plan->h_dets[det].eps, plan->h_dets[det].zeta,
+                                                 (float*)grad_grids, accumulate, s));
     return PISCO_OK;
 }
 
@@ -708,18 +724,18 @@ extern "C" pisco_status pisco_adjoint_sky_beam(pisco_plan* plan, int det, int64_
         return PISCO_EINVAL;
     }
     cudaStream_t s = (cudaStream_t)stream;
-    const size_t bytes = folded_grad_bytes(plan->grid_n, 0);
+    const size_t bytes = plan_grad_scratch_bytes(plan);
     if (!plan->d_gscratch) PISCO_CUDA(plan, cudaMalloc(&plan->d_gscratch, bytes));
     PISCO_CUDA(plan, cudaMemsetAsync(plan->d_gscratch, 0, bytes, s));
     if (!accumulate) PISCO_CUDA(plan, cudaMemsetAsync(maps, 0, 3 * (size_t)plan->npix * sizeof(float), s));
     if (n > 0) {
         const int64_t begin = 0, count = n;
         st = run(plan, kBoth, det, 1, &begin, &count, theta, phi, psi, maps, tod, nullptr, s, nullptr,
-                 plan->d_gscratch);
+                 plan->d_gscratch, 1);
         if (st != PISCO_OK) return st;
     }
-    PISCO_CUDA(plan, launch_unfold_grid(plan->d_gscratch, plan->grid_n, plan->h_dets[det].eps,
-                                        plan->h_dets[det].zeta, grad_grids, accumulate, 0, s));
+    PISCO_CUDA(plan, launch_unfold_coef_grid((const float*)plan->d_gscratch, plan->grid_n, plan->h_dets[det].eps,
+                                             plan->h_dets[det].zeta, (float*)grad_grids, accumulate, s));
     return PISCO_OK;
 }
 

@@ -67,22 +67,37 @@ static __device__ __forceinline__ float rcp_approx(float x) {
     return r;
 }
 
-// Add the 12 accumulated node gradients of one cell (maps A, Bq', Cu' x nodes
-// (i, j), (i+1, j), (i, j+1), (i+1, j+1)) to the folded gradient and clear them.
-// The FP32 folded gradient is interleaved per node, [N][N][4] = (A, Bq', Cu', 0),
-// so each node takes one 16-byte vector reduction instead of three scalar atomics.
-static __device__ __forceinline__ void red_add_v4(float* p, float a, float b, float c) {
-    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(0.f)
+// Add the 12 accumulated gradients of one cell to the folded gradient and clear
+// them.  Two layouts of the FP32 folded gradient:
+//  * per node, [N][N][4] = (A, Bq', Cu', 0): gw holds the gradients of the four
+//    nodes (i, j), (i+1, j), (i, j+1), (i+1, j+1) of each map, one 16-byte
+//    vector reduction per node;
+//  * per cell, [(N-1)^2][3][4]: gw holds, per map, the gradients of the cell's
+//    bilinear coefficients (c0, c1, c2, c3) of f = c0 + c1 fx + c2 fy + c3 fx fy,
+//    one 16-byte vector reduction per map (3 instead of 4); the unfolding
+//    kernel turns them into node gradients.
+static __device__ __forceinline__ void red_add_v4(float* p, float a, float b, float c, float d) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d)
                  : "memory");
 }
 
-static __device__ __forceinline__ void flush_grid(float* g, int cell, int nc, int n, float* gw) {
+static __device__ __forceinline__ void flush_grid(float* g, int cell, int nc, int n, float* gw, int coef) {
+    if (coef) {
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+            if (gw[4 * m] != 0.f || gw[4 * m + 1] != 0.f || gw[4 * m + 2] != 0.f || gw[4 * m + 3] != 0.f)
+                red_add_v4(g + 12 * (long long)cell + 4 * m, gw[4 * m], gw[4 * m + 1], gw[4 * m + 2], gw[4 * m + 3]);
+            gw[4 * m] = gw[4 * m + 1] = gw[4 * m + 2] = gw[4 * m + 3] = 0.f;
+        }
+        return;
+    }
     const int i = cell % nc, j = cell / nc;
     const long long base = (long long)j * n + i;
     const long long off[4] = {base, base + 1, base + n, base + n + 1};
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        if (gw[k] != 0.f || gw[4 + k] != 0.f || gw[8 + k] != 0.f) red_add_v4(g + 4 * off[k], gw[k], gw[4 + k], gw[8 + k]);
+        if (gw[k] != 0.f || gw[4 + k] != 0.f || gw[8 + k] != 0.f)
+            red_add_v4(g + 4 * off[k], gw[k], gw[4 + k], gw[8 + k], 0.f);
         gw[k] = gw[4 + k] = gw[8 + k] = 0.f;
     }
 }
@@ -452,7 +467,7 @@ __global__ void __launch_bounds__(NT, fast_min_blocks(MODE)) k_fast(const __grid
                             if (MODE == kGrid || MODE == kBoth) {
                                 const int cell = (int)flv * nc + (int)flu;
                                 if (cell != gcell[p4]) {
-                                    if (gcell[p4] >= 0) flush_grid(gout, gcell[p4], nc, P.grid_n, gw[p4]);
+                                    if (gcell[p4] >= 0) flush_grid(gout, gcell[p4], nc, P.grid_n, gw[p4], P.grid_coef);
                                     gcell[p4] = cell;
                                 }
                                 const float q = rcp_approx(2.f - w);
@@ -465,8 +480,11 @@ __global__ void __launch_bounds__(NT, fast_min_blocks(MODE)) k_fast(const __grid
                                 const float cA = yv * ip[p4];
                                 const float cB = yv * fmaf(re, qp[p4], -2.f * im2 * up[p4]);
                                 const float cC = yv * fmaf(2.f * im2, qp[p4], re * up[p4]);
-                                const float w11 = fx * fy, w10 = fx - w11, w01 = fy - w11;
-                                const float w00 = (1.f - fx) - w01;
+                                // node weights, or the bilinear coefficients' weights (1, fx, fy, fx fy)
+                                const float w11 = fx * fy;
+                                const bool cf = P.grid_coef != 0;
+                                const float w10 = cf ? fx : fx - w11, w01 = cf ? fy : fy - w11;
+                                const float w00 = cf ? 1.f : (1.f - fx) - (fy - w11);
                                 const float wt[4] = {w00, w10, w01, w11};
 #pragma unroll
                                 for (int k = 0; k < 4; ++k) {
@@ -542,7 +560,7 @@ __global__ void __launch_bounds__(NT, fast_min_blocks(MODE)) k_fast(const __grid
                     if (MODE == kGrid || MODE == kBoth) {
 #pragma unroll
                         for (int p4 = 0; p4 < NP; ++p4)
-                            if (gcell[p4] >= 0) flush_grid(gout, gcell[p4], nc, P.grid_n, gw[p4]);
+                            if (gcell[p4] >= 0) flush_grid(gout, gcell[p4], nc, P.grid_n, gw[p4], P.grid_coef);
                     }
                     if (MODE == kAdjoint || MODE == kBoth) {
                         float* maps = (float*)P.out;

@@ -65,6 +65,7 @@ struct LaunchParams {
     int32_t* counts;       // count mode output
     int* err;
     void* out2;            // sky and beam-grid transposes in one pass: the folded beam-grid gradient
+    int grid_coef;         // FP32 folded gradient per cell coefficient ([(N-1)^2][3][4]) instead of per node
     int n_real;            // multi-realization plans: realizations per pixel
     int n_zeta;            // shared-geometry pass: number of polarisation angles
     long long out_stride;  // shared-geometry pass: elements between the TODs of two angles
@@ -124,13 +125,16 @@ pisco_status check_pointing(pisco_plan* plan, int64_t n, const double* a, const 
 // Launch one path over detectors [d0, d0 + nd) with per-detector sample ranges.
 pisco_status run(pisco_plan* plan, int mode, int d0, int nd, const int64_t* begin, const int64_t* count,
                  const double* theta, const double* phi, const double* psi, void* out, const void* tod_in,
-                 int32_t* counts, cudaStream_t s, const PsbAngles* psb = nullptr, void* out2 = nullptr);
+                 int32_t* counts, cudaStream_t s, const PsbAngles* psb = nullptr, void* out2 = nullptr,
+                 int grid_coef = 0);
 
 // Bytes of the folded beam-grid gradient scratch: FP32 plans interleave the three
 // folded maps per node with a pad ([N][N][4] floats), the plain path keeps [3][N][N] doubles.
 inline size_t folded_grad_bytes(int grid_n, int f64) {
     return (size_t)grid_n * grid_n * (f64 ? 3 * sizeof(double) : 4 * sizeof(float));
 }
+// The same gradient per cell coefficient (FP32 plans' own scratch): [(N-1)^2][3][4] floats.
+inline size_t folded_coef_grad_bytes(int grid_n) { return (size_t)(grid_n - 1) * (grid_n - 1) * 12 * sizeof(float); }
 
 // Launchers (defined in the kernel translation units).
 cudaError_t launch_fast_texture(const LaunchParams& p, int mode, int tile_samples, int np, cudaStream_t s);
@@ -142,6 +146,8 @@ cudaError_t launch_plan_kernels(pisco_plan* plan, const void* sky, int sky_dtype
                                 const float* grids, cudaStream_t s, double* d_omega_out);
 cudaError_t launch_fold_nodes32(const float* grids, int n, double eps, double zeta, float* out3, cudaStream_t s);
 cudaError_t launch_beam_kernels(pisco_plan* plan, const float* grids, cudaStream_t s, double* d_omega_out);
+cudaError_t launch_unfold_coef_grid(const float* cgrad, int n, double eps, double zeta, float* grad, int accumulate,
+                                   cudaStream_t s);
 cudaError_t launch_unfold_grid(const void* folded, int n, double eps, double zeta, void* grad, int accumulate,
                                int f64, cudaStream_t s);
 cudaError_t launch_omega_adjoint(const void* tod, const void* y, long long n, int f64, double omega, double scale_tod,

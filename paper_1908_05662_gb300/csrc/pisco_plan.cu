@@ -295,6 +295,55 @@ __global__ void k_omega_adjoint(const T* __restrict__ tod, const T* __restrict__
     }
 }
 
+// Per-cell coefficient gradients G[cell][m] = dL/d(c0, c1, c2, c3) to the six input
+// maps.  With c0 = f00, c1 = f10 - f00, c2 = f01 - f00, c3 = f11 - f10 - f01 + f00,
+// node (i, j) collects g0 - g1 - g2 + g3 from cell (i, j) (its f00), g1 - g3 from
+// cell (i-1, j) (f10), g2 - g3 from cell (i, j-1) (f01) and g3 from cell (i-1, j-1)
+// (f11); then the transpose of the folding as in k_unfold.
+__global__ void k_unfold_coef(const float* __restrict__ cg, int n, double eps, double zeta, float* __restrict__ g,
+                              int accumulate) {
+    const long long nn = (long long)n * n;
+    const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= nn) return;
+    const int nc = n - 1;
+    const int i = (int)(idx % n), j = (int)(idx / n);
+    double node[3] = {0.0, 0.0, 0.0};
+    for (int m = 0; m < 3; ++m) {
+        double v = 0.0;
+        if (i < nc && j < nc) {
+            const float* c = cg + 12 * ((long long)j * nc + i) + 4 * m;
+            v += (double)c[0] - (double)c[1] - (double)c[2] + (double)c[3];
+        }
+        if (i > 0 && j < nc) {
+            const float* c = cg + 12 * ((long long)j * nc + i - 1) + 4 * m;
+            v += (double)c[1] - (double)c[3];
+        }
+        if (i < nc && j > 0) {
+            const float* c = cg + 12 * ((long long)(j - 1) * nc + i) + 4 * m;
+            v += (double)c[2] - (double)c[3];
+        }
+        if (i > 0 && j > 0) v += (double)cg[12 * ((long long)(j - 1) * nc + i - 1) + 4 * m + 3];
+        node[m] = v;
+    }
+    double s2z, c2z;
+    sincos(2.0 * zeta, &s2z, &c2z);
+    const double gbq = c2z * node[1] + s2z * node[2];  // transpose of the 2 zeta rotation
+    const double gcu = -s2z * node[1] + c2z * node[2];
+    const double v[6] = {(1.0 + eps) * node[0], (1.0 + eps) * gbq, (1.0 + eps) * gcu,
+                         (1.0 - eps) * node[0], (1.0 - eps) * gbq, (1.0 - eps) * gcu};
+#pragma unroll
+    for (int e = 0; e < 6; ++e) {
+        const float add = (float)v[e];
+        g[e * nn + idx] = accumulate ? g[e * nn + idx] + add : add;
+    }
+}
+
+cudaError_t launch_unfold_coef_grid(const float* cgrad, int n, double eps, double zeta, float* grad, int accumulate,
+                                   cudaStream_t s) {
+    k_unfold_coef<<<blocks_for((long long)n * n, 256), 256, 0, s>>>(cgrad, n, eps, zeta, grad, accumulate);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_unfold_grid(const void* folded, int n, double eps, double zeta, void* grad, int accumulate,
                                int f64, cudaStream_t s) {
     const unsigned b = blocks_for((long long)n * n, 256);
