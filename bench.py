@@ -150,8 +150,9 @@ def cached_sky(nside, seed, device):
         return torch.load(path, map_location=device)
     sky = sy.gaussian_sky(nside, seed, device=device)
     os.makedirs(os.path.dirname(path), exist_ok=True)
-    torch.save(sky, path + ".tmp")
-    os.replace(path + ".tmp", path)
+    tmp = f"{path}.{os.getpid()}.tmp"  # ranks of one machine may write it at the same time
+    torch.save(sky, tmp)
+    os.replace(tmp, path)
     return sky
 
 
