@@ -275,3 +275,51 @@ def test_fp32_single_detector_workload_sampled():
     assert abs(omega / ob.omega_tilde(grids[0].astype(np.float64), r) - 1) < 1e-12
     np.testing.assert_array_less(np.abs(out[idx] - ref), 2e-6 * mag)
     assert np.max(np.abs(out[idx] - ref)) <= 1e-6 * np.max(np.abs(ref))
+
+
+def test_focal_plane_configuration_batched_sampled():
+    """The focal-plane configuration (64 detectors with their own offsets, FWHM 1.2-1.8 deg,
+    ellipticity 0-0.1 and 201^2 grids of radius 6 deg, nside 256 sky) in the benchmark's launch:
+    one pisco_convolve_batched call over uneven scan lengths; three samples of every detector
+    checked against the oracle."""
+    nside, r, n_det = 256, math.radians(6.0), 64
+    sky = sy.gaussian_sky(nside, 1, device=DEV)
+    off, fwhm, ell, zeta = sy.focal_plane(n_det, 3)
+    grids = np.stack([sy.gaussian_beam_maps(201, r, fwhm[d], ellipticity=ell[d]) for d in range(n_det)])
+    dets = [(float(zeta[d]), 0.0, 1.0) for d in range(n_det)]
+    lengths = np.random.default_rng(4).integers(200, 3001, n_det)
+    parts = [sy.ces_scan(int(lengths[d]), offset=tuple(off[d]), device=DEV) for d in range(n_det)]
+    th, ph, ps = (torch.cat([p[k] for p in parts]).contiguous() for k in range(3))
+    offsets = [0] + list(np.cumsum(lengths))
+    with pisco.Plan(nside, r, sky, dets, torch.as_tensor(grids, device=DEV).contiguous()) as plan:
+        out = plan.convolve_batched(offsets, th, ph, ps).double().cpu().numpy()
+        omegas = [plan.omega(d)[0] for d in range(n_det)]
+        plan.sync_status()
+    skyn, thn, phn, psn = sky.cpu().numpy(), th.cpu().numpy(), ph.cpu().numpy(), ps.cpu().numpy()
+    for d in range(n_det):
+        idx = offsets[d] + np.array([0, lengths[d] // 2, lengths[d] - 1])
+        ref, mag = _oracle(nside, r, skyn, grids[d], dets[d], thn[idx], phn[idx], psn[idx], omegas[d])
+        np.testing.assert_array_less(np.abs(out[idx] - ref), 2e-6 * mag)
+
+
+def test_differentiation_configuration_transposes_dot_identities():
+    """The differentiation configuration (nside 512, parametric beam on a 201^2 grid of radius
+    5 deg) at full resolution on 1e6 azimuth-scan samples: the sky and beam-grid transposes
+    satisfy <A_S s, y> = <s, A_S^T y> and <A_G G, y> = <G, A_G^T y> (Omega~ held fixed, where
+    the TOD is linear in the grids), all sums from the GPU, to FP32 accumulation accuracy."""
+    from paper_1908_05662_gb300 import beams
+    nside, r, n = 512, math.radians(5.0), 1_000_000
+    sky = sy.gaussian_sky(nside, 1, device=DEV)
+    g = beams.gaussian_beam_grids(201, r, 1.5, 0.05, 0.005, device=DEV).float()[None].contiguous()
+    th, ph, ps = (a.contiguous() for a in sy.ces_scan(n, device=DEV))
+    y = torch.randn(n, device=DEV, generator=torch.Generator(device=DEV).manual_seed(5))
+    with pisco.Plan(nside, r, sky, [(0.2, 0.01, 1.0)], g, omega_tilde=[0.002]) as plan:
+        d = plan.convolve(th, ph, ps).double()
+        maps, grad = plan.adjoint_sky_beam(th, ph, ps, y)
+        plan.sync_status()
+    lhs = torch.dot(d, y.double()).item()
+    scale = torch.sum(torch.abs(d * y.double())).item()
+    rhs_sky = torch.sum(sky.double() * maps.double()).item()
+    rhs_grid = torch.sum(g[0].double() * grad.double()).item()
+    assert abs(lhs - rhs_sky) <= 1e-5 * scale, (lhs, rhs_sky)
+    assert abs(lhs - rhs_grid) <= 1e-5 * scale, (lhs, rhs_grid)
