@@ -65,8 +65,10 @@ typedef enum pisco_status {
 enum {
     PISCO_FP64_PLAIN = 0, /* FP64 throughout, one CTA per sample: the plain reference path */
     PISCO_FP32 = 1,       /* FP32 arithmetic, FP64 only where offsets would cancel */
-    PISCO_BF16_MR = 2,    /* n_real sky realizations in BF16, FP32 weights rounded to BF16, tensor cores, FP32 accumulate */
-    PISCO_FP16_MR = 3     /* the same with FP16 realizations and weights */
+    PISCO_BF16_MR = 2,    /* n_real sky realizations in BF16; FP32 weights split into two BF16 parts (hi + lo);
+                             fifth-generation tensor cores (tcgen05), FP32 accumulate in tensor memory;
+                             128-sample tiles */
+    PISCO_FP16_MR = 3     /* the same with FP16 realizations and weight parts */
 };
 
 /* Element type of caller arrays (sky_dtype). */

@@ -1,5 +1,5 @@
 // C ABI: argument validation, plan lifetime and launches.  The arithmetic
-// lives in the kernels (pisco_plan.cu, pisco_fast.cu, pisco_plain.cu).
+// lives in the kernels (pisco_plan.cu, pisco_fast.cuh, pisco_plain.cu, pisco_mr.cu).
 
 #include "pisco_internal.cuh"
 
