@@ -139,3 +139,24 @@ def test_multirealization_invalid_samples_and_unsupported_calls():
     with pytest.raises(pisco.PiscoError):
         bad = torch.zeros(hp.npix(nside), 3, 48, dtype=torch.bfloat16, device=DEV)
         pisco.Plan(nside, r, bad, [(0, 0, 1)], grids, precision=pisco.PISCO_BF16_MR)
+
+
+def test_multirealization_batched_detectors_equal_single_calls_and_empty_input():
+    """Two detectors with their own beams in one pisco_convolve_batched launch (128-sample tiles
+    of each detector's range, uneven lengths) give the same TOD as one call per detector, and an
+    empty input is a no-op."""
+    nside, r, n_real = 32, math.radians(8.0), 64
+    stack, _ = _stack(nside, n_real, torch.bfloat16, 21)
+    grids = torch.as_tensor(np.stack([sy.random_beam_maps(41, 31), sy.random_beam_maps(41, 32)]), device=DEV)
+    dets = [(0.2, 0.01, 1.0), (1.3, 0.03, 0.9)]
+    th, ph, ps = sy.raster_scan(330, center=(1.1, 2.0), half_size=math.radians(4.0), rows=5)
+    offsets = [0, 130, 330]
+    with pisco.Plan(nside, r, stack, dets, grids, precision=pisco.PISCO_BF16_MR) as plan:
+        both = plan.convolve_batched(offsets, _t(th), _t(ph), _t(ps)).cpu()
+        for d in range(2):
+            a, b = offsets[d], offsets[d + 1]
+            one = plan.convolve(_t(th[a:b]), _t(ph[a:b]), _t(ps[a:b]), det=d).cpu()
+            torch.testing.assert_close(both[a:b], one, rtol=0, atol=0)
+        empty = torch.empty(0, dtype=torch.float64, device=DEV)
+        assert plan.convolve(empty, empty, empty).shape == (0, n_real)
+        plan.sync_status()
