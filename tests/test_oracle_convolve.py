@@ -238,3 +238,22 @@ def test_nan_pointing_gives_nan():
     grids = sy.random_beam_maps(11, 1).astype(np.float64)
     d = oc.tod(nside, r, np.ones((3, hp.npix(nside))), grids, (0, 0, 1), 1.0, [np.nan, 1.0], [0.0, 0.0], [0.0, 0.0])
     assert np.isnan(d[0]) and np.isfinite(d[1])
+
+
+def test_worker_processes_reproduce_the_oracle():
+    """The multi-process harness that times the oracle on all host cores returns exactly what
+    one call of the oracle gives for the samples it processed."""
+    from oracle import parallel as op
+    nside, r = 8, math.radians(20.0)
+    grids = sy.random_beam_maps(21, 4).astype(np.float64)
+    det = (0.2, 0.05, 1.0)
+    omega = ob.omega_tilde(grids[0], r)
+    sky = sy.white_sky(nside, 3).numpy()
+    th, ph, ps = sy.random_pointings(9, 6)
+    idx, d, span, used = op.tod_sampled(nside, r, sky, grids, det, omega, th, ph, ps, processes=3, budget_s=1e9)
+    assert used == 3 and span > 0
+    np.testing.assert_array_equal(idx, np.arange(9))
+    np.testing.assert_array_equal(d, oc.tod(nside, r, sky, grids, det, omega, th, ph, ps))
+    idx, d, _, _ = op.tod_sampled(nside, r, sky, grids, det, omega, th, ph, ps, processes=2, max_per_worker=2)
+    np.testing.assert_array_equal(idx, [0, 1, 4, 5])
+    np.testing.assert_array_equal(d, oc.tod(nside, r, sky, grids, det, omega, th[idx], ph[idx], ps[idx]))
