@@ -53,6 +53,12 @@ WORKLOAD = dict(workload="single-detector FP32: nside 512 sky, 1.5 deg beam + 1%
 FLOPS_PER_PAIR = 78
 # FP32 peak of the GPU from unit counts: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+# DRAM bytes (read + write) of one forward launch on the default single-detector workload
+# (1e7 samples, 16-sample tiles, 1 pixel per thread, 64-byte cells) from one ncu capture of
+# dram__bytes_read.sum + dram__bytes_write.sum (1 pass, full-size launch): 486.63 MB read,
+# 47.03 MB written.  Pointing (240 MB) and TOD (40 MB) stream through once; the rest is the
+# L2-resident sky and beam cells, some re-read after the pointing stream evicts them.
+FORWARD_TRAFFIC_BYTES = {(10_000_000, 16, 1): 486.63e6 + 47.03e6}
 
 
 def parse():
@@ -721,7 +727,9 @@ def main():
                        "pairs_per_step": pairs * world, "mean_disc_pixels": pairs / n,
                        "l2": "inputs larger than L2 (pointing 24 B/sample = 240 MB)"},
             "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": FP32_PEAK_TFLOPS,
-                         "unit": "TFLOP/s", "frac": achieved_tflops / FP32_PEAK_TFLOPS, "traffic": None,
+                         "unit": "TFLOP/s", "frac": achieved_tflops / FP32_PEAK_TFLOPS,
+                         "traffic": FORWARD_TRAFFIC_BYTES.get((n, tuned[0], tuned[1])),
+                         "traffic_note": "ncu DRAM bytes read + written per forward launch",
                          "kernel": f"pisco::k_fast<{tuned[0]}, {tuned[1]}, cells, forward>",
                          "peak_note": "FP32 from unit counts: 152 SM x 128 lanes x 2 x 2070 MHz",
                          "hbm_frac_of_measured": (28 * n / (ms / 1e3)) / 6758.2e9},
