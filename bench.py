@@ -285,6 +285,30 @@ def run_focalplane(args, dev):
     with ClockSampler(torch.cuda.current_device()) as clocks:
         ms = _event_time(step, args.steps, args.warmup, stream)
     plan.sync_status()
+    # the plain FP64 path (one batched call) on the first 2000 samples of every detector
+    m = 2000
+    idx = torch.cat([torch.arange(offsets[d], offsets[d] + min(m, int(lengths[d])), device=dev)
+                     for d in range(n_det)])
+    sub_off = [0] + list(np.cumsum([min(m, int(x)) for x in lengths]))
+    thp, php, psp = th[idx].contiguous(), ph[idx].contiguous(), ps[idx].contiguous()
+    grids_t = torch.as_tensor(grids, device=dev).contiguous()
+    with pisco.Plan(nside, r, sky, dets, grids_t, precision=pisco.PISCO_FP64_PLAIN) as plain:
+        tod64 = torch.empty(len(idx), dtype=torch.float64, device=dev)
+        ms_plain = _event_time(lambda: plain.convolve_batched(sub_off, thp, php, psp, out=tod64), 2, 1, stream)
+        plain.sync_status()
+    plain_rate = len(idx) / (ms_plain / 1e3)
+    fp32_vs_64 = ((tod[idx].double() - tod64).abs().max() / tod64.abs().max()).item()
+    # the FP64 oracle on the first sample of every detector
+    from oracle import beam as ob
+    from oracle import convolve as oc
+    skyn = sky.cpu().numpy()
+    first = np.asarray(offsets[:-1], np.int64)
+    thn, phn, psn = (a[torch.as_tensor(first, device=dev)].cpu().numpy() for a in (th, ph, ps))
+    ref = np.array([oc.tod(nside, r, skyn, grids[d].astype(np.float64), dets[d],
+                           ob.omega_tilde(grids[d][0].astype(np.float64), r), thn[d:d + 1], phn[d:d + 1],
+                           psn[d:d + 1])[0] for d in range(n_det)])
+    got = tod[torch.as_tensor(first, device=dev)].double().cpu().numpy()
+    err_oracle = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
     achieved = FLOPS_PER_PAIR * pairs / (ms / 1e3) / 1e12
     out = {"metric": "TOD samples/s (64-detector focal plane, nside 256, R 6 deg, 201^2 grids)",
            "value": n / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
@@ -296,6 +320,12 @@ def run_focalplane(args, dev):
                       "l2": "inputs larger than L2"},
            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                         "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None},
+           "plain_fp64_gpu": {"value": plain_rate, "unit": UNIT, "samples_timed": len(idx),
+                              "sample": f"first {m} samples of each detector, one batched call",
+                              "speedup_of_fp32": (n / (ms / 1e3)) / plain_rate,
+                              "fp32_vs_fp64_normwise": fp32_vs_64},
+           "err_vs_oracle_normwise": err_oracle,
+           "oracle_sample": "first sample of each of the 64 detectors",
            "gpu_launches": args.steps, "clocks": clocks.summary()}
     if graph is None:
         out["graph_error"] = graph_error
@@ -329,8 +359,21 @@ def run_multireal(args, dev):
         plan.sync_status()
         results[name] = (ms, clocks.summary(), out[::20000].double().cpu().numpy())
         plan.close()
-    pairs = int(pisco.Plan(nside, r, exact[:, :, 0].T.contiguous(), [det], g).disc_count(th, ph)
-                .to(torch.int64).sum().item())
+    # one realization through the plain FP64 path (first 1e5 samples) and the FP32 path (all
+    # samples): the per-realization cost of running the stack through them one by one
+    sky0 = exact[:, :, 0].T.contiguous()
+    m = min(n, 100_000)
+    with pisco.Plan(nside, r, sky0, [det], g, precision=pisco.PISCO_FP64_PLAIN) as plain:
+        tod64 = torch.empty(m, dtype=torch.float64, device=dev)
+        ms_plain = _event_time(lambda: plain.convolve(th[:m], ph[:m], ps[:m], out=tod64), 2, 1, stream)
+        plain.sync_status()
+    with pisco.Plan(nside, r, sky0, [det], g) as fp32:
+        tod32 = torch.empty(n, dtype=torch.float32, device=dev)
+        ms_fp32 = _event_time(lambda: fp32.convolve(th, ph, ps, out=tod32), 2, 1, stream)
+        pairs = int(fp32.disc_count(th, ph).to(torch.int64).sum().item())
+        fp32.sync_status()
+    plain_rate = m / (ms_plain / 1e3) / n_real  # samples/s with all realizations
+    fp32_rate = n / (ms_fp32 / 1e3) / n_real
     # error against the FP64 oracle on the unrounded realizations, every 20000th sample
     from oracle import beam as ob
     from oracle import convolve as oc
@@ -358,6 +401,12 @@ def run_multireal(args, dev):
         "realization_samples_per_s": n * n_real / (ms / 1e3),
         "fp16": {"ms_per_step": results["fp16"][0], "value": n / (results["fp16"][0] / 1e3)},
         "err_vs_oracle_normwise_per_realization": errs,
+        "plain_fp64_gpu": {"value": plain_rate, "unit": UNIT, "samples_timed": m, "realizations_timed": 1,
+                           "note": "one realization timed, samples/s divided by the 256 realizations",
+                           "speedup_of_bf16": (n / (ms / 1e3)) / plain_rate},
+        "fp32_per_realization": {"value": fp32_rate, "unit": UNIT, "realizations_timed": 1,
+                                 "note": "FP32 path, one realization per pass, divided by 256",
+                                 "speedup_of_bf16": (n / (ms / 1e3)) / fp32_rate},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": 1927.2, "unit": "TFLOP/s",
                      "frac": achieved / 1927.2, "traffic": None,
                      "note": "algorithmic 2*3*pairs*R flops (the hi/lo weight split doubles the issued MMAs); "
@@ -513,6 +562,17 @@ def run_grad(args, dev):
                  "sky_and_beam_adjoint_ms": _event_time(lambda: plan.adjoint_sky_beam(th, ph, ps, y), 2, 1, stream)}
         pairs = int(plan.disc_count(th, ph).to(torch.int64).sum().item())
         plan.sync_status()
+    m = min(n, 100_000)
+    y64 = y[:m].double()
+    with pisco.Plan(nside, r, sky, [det], g, precision=pisco.PISCO_FP64_PLAIN) as plain:
+        t, p_, q = th[:m], ph[:m], ps[:m]
+        plain_ms = {"forward_ms": _event_time(lambda: plain.convolve(t, p_, q), 2, 1, stream),
+                    "sky_adjoint_ms": _event_time(lambda: plain.adjoint(t, p_, q, y64), 2, 1, stream),
+                    "beam_grid_adjoint_ms": _event_time(lambda: plain.beam_grid_adjoint(t, p_, q, y64), 2, 1,
+                                                        stream)}
+        plain.sync_status()
+    plain_step_per_sample = sum(plain_ms.values()) / m
+    fp32_step_per_sample = (parts["forward_ms"] + parts["sky_and_beam_adjoint_ms"]) / n
     # gradient check on a slice against the FP64 oracle
     # (the slice's target is the oracle's TOD of the perturbed parameters, on both sides)
     k = 48
@@ -547,7 +607,13 @@ def run_grad(args, dev):
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": "differentiation: nside 512, parametric beam (FWHM 1.5 deg, e 0.05, l 0.005), "
                                   "R 5 deg, 201^2 grid, 1e7 scan samples", "samples": n, "pairs_per_pass": pairs},
-           "passes": parts, "grad_vs_oracle_fd_rel": rel, "grad": list(map(float, grad)), "fd": fd,
+           "passes": parts,
+           "plain_fp64_gpu": {"passes_ms": plain_ms, "samples_timed": m,
+                              "samples_per_s": 1e3 / plain_step_per_sample,
+                              "speedup_of_fp32_passes": plain_step_per_sample / fp32_step_per_sample,
+                              "note": "forward + sky adjoint + beam-grid adjoint per sample, against the FP32 "
+                                      "forward + fused sky-and-beam adjoint"},
+           "grad_vs_oracle_fd_rel": rel, "grad": list(map(float, grad)), "fd": fd,
            "roofline": {"bound": "alu", "kernel": "pisco::k_fast<16, sky and beam-grid transposes>",
                         "achieved": FLOPS_PER_PAIR * pairs / (bg / 1e3) / 1e12, "peak": FP32_PEAK_TFLOPS,
                         "unit": "TFLOP/s", "frac": FLOPS_PER_PAIR * pairs / (bg / 1e3) / 1e12 / FP32_PEAK_TFLOPS,
