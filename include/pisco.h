@@ -67,7 +67,9 @@ enum {
     PISCO_FP32 = 1,       /* FP32 arithmetic, FP64 only where offsets would cancel */
     PISCO_BF16_MR = 2,    /* n_real sky realizations in BF16; FP32 weights split into two BF16 parts (hi + lo);
                              fifth-generation tensor cores (tcgen05), FP32 accumulate in tensor memory;
-                             128-sample tiles */
+                             realization rows gathered into shared memory by TMA; 128-sample tiles.
+                             Realization values must be finite: every pixel of a tile's disc union
+                             enters the contraction, with weight zero outside a sample's disc */
     PISCO_FP16_MR = 3     /* the same with FP16 realizations and weight parts */
 };
 
@@ -109,7 +111,7 @@ typedef struct pisco_plan pisco_plan;  /* opaque, owned by the library */
  *
  * Sec. 5.1: PISCO receives the sky maps, the beamsor and the focal plane
  * (zeta per detector); Sec. 5.2's beam interpolation grid is assembled here.
- *   nside        HEALPix resolution, 1 <= nside <= 8192.
+ *   nside        HEALPix resolution, 1 <= nside <= 8192 (<= 7723 for PISCO_*_MR plans).
  *   radius_rad   disc cut-off rho_max (Sec. 5.3, Table 1) = beam grid radius,
  *                0 < radius < pi/2.
  *   sky          device, [3][12 nside^2] of sky_dtype (I, Q, U; V is zero, Sec. 6.2);

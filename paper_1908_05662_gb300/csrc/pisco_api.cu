@@ -3,6 +3,7 @@
 
 #include "pisco_internal.cuh"
 
+#include <climits>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -164,6 +165,11 @@ extern "C" pisco_status pisco_plan_create(pisco_plan** out, int nside, double ra
     const int n_real = mr ? opt->n_real : 1;
     if (mr && !(n_real >= 32 && n_real <= 256 && n_real % 32 == 0)) {
         set_error(nullptr, "n_real %d is not a multiple of 32 in [32, 256]", n_real);
+        return PISCO_EINVAL;
+    }
+    if (mr && 36LL * nside * nside >= INT_MAX) {
+        // the tensor-core kernel addresses the stack's 3 Npix rows with 32-bit TMA coordinates
+        set_error(nullptr, "multi-realization plans take nside <= 7723 (got %d)", nside);
         return PISCO_EINVAL;
     }
     if (n_det < 1 || !dets) {

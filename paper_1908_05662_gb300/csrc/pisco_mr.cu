@@ -11,9 +11,14 @@
 // the tile.  The CTA traverses the union of the 128 discs ring by ring (the
 // ring-ordered disc query of the FP32 kernel) and, per batch of 16 union
 // pixels (K = 48: pixel x I, Q, U):
-//   1. copies the realization rows [pixel][I,Q,U][R] (16-bit) with 16-byte
-//      asynchronous copies straight into the B operand's MN-major core-matrix
-//      layout (8 k-rows x 16 bytes per core matrix, no swizzle);
+//   1. copies the realization rows [pixel][I,Q,U][R] (16-bit) straight into
+//      the B operand's MN-major core-matrix layout (8 k-rows x 16 bytes per
+//      core matrix, no swizzle): a core matrix whose 8 rows are consecutive
+//      in the stack (pixels of one ring run) comes by TMA: one 3-D tile load
+//      per 8-row block fills its core matrices for all realizations (8 rows x
+//      R realizations, completing on the buffer's load mbarrier); blocks with
+//      a run boundary inside, or in the batch's tail, are 16-byte asynchronous
+//      copies and zeros;
 //   2. computes the 128 x 16 pair weights in FP32 (zero outside a sample's
 //      disc) and splits each into two 16-bit parts, W = W_hi + W_lo
 //      (W_lo the rounded remainder), written in the A operand's K-major
@@ -22,8 +27,9 @@
 //      W_hi and W_lo over the three K-steps of 16, then tcgen05.commit to the
 //      batch buffer's mbarrier.
 // Operand buffers are double-buffered: the MMAs of one batch run while the
-// threads copy and weigh the next; a buffer is rewritten only after the
-// mbarrier of the MMAs that read it has completed.  At the end of the tile
+// TMA loads and the threads' weights fill the next; a buffer is rewritten only
+// after the mbarrier of the MMAs that read it has completed, and its MMAs are
+// issued only after its load mbarrier has.  At the end of the tile
 // the sixteen warps read the accumulator rows back with tcgen05.ld (warp w
 // sees TMEM lanes 32 (w % 4) ..; warps w, w + 4, w + 8, w + 12 take a quarter
 // of the realizations each) and store d[t][r] = scale * D[t][r].  Every wait on an mbarrier is
@@ -34,6 +40,7 @@
 
 #include "pisco_internal.cuh"
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -128,6 +135,22 @@ __device__ __forceinline__ void mma_commit(unsigned long long* bar) {
                  : "memory");
 }
 
+// The calling thread arrives on the mbarrier and raises its expected transaction count by `bytes`.
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// TMA tile load of a 3-D tensor's box at coordinates (0, y, 0) into dst, which must
+// be 128-byte aligned; completes `bar`'s transaction count by the box's bytes.
+__device__ __forceinline__ void tma_tile3(void* dst, const CUtensorMap* map, int y, unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+        "l"((unsigned long long)map), "r"(0), "r"(y), "r"(0), "r"(smem_u32(bar))
+        : "memory");
+}
+
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
@@ -136,7 +159,7 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
 __device__ __forceinline__ void batch_pixel(int b0, int tid, int nr, int total, const int* sPref, const int* sJlo,
                                             const int* sRc, const int* sJref, const float* sDph, const float* sAref,
                                             const int* sFirst, int* bRi, int* bJw, int* bOk, float* bSa, float* bCa,
-                                            long long* bPix) {
+                                            long long* bPix, unsigned* bFlag) {
     const int f = b0 + tid;
     int ok = f < total;
     int ri = 0, jw = 0;
@@ -156,12 +179,28 @@ __device__ __forceinline__ void batch_pixel(int b0, int tid, int nr, int total, 
         const float aa = fmaf((float)(j - sJref[ri]), sDph[ri], sAref[ri]);
         sincosf(0.5f * aa, &sa, &ca);
     }
+    const long long pix = ok ? (long long)sFirst[ri] + jw : 0;
     bRi[tid] = ri;
     bJw[tid] = jw;
     bOk[tid] = ok;
     bSa[tid] = sa;
     bCa[tid] = ca;
-    bPix[tid] = ok ? (long long)sFirst[ri] + jw : 0;
+    bPix[tid] = pix;
+    // core matrix kb holds rows k = 8 kb .. 8 kb + 7 (k = 3 p + m): one TMA tile when its
+    // pixels are valid and consecutive in the stack (rows 3 pix + m then run on)
+    const long long nxt = __shfl_down_sync(0xffffu, pix, 1, KPIX);
+    const unsigned okm = __ballot_sync(0xffffu, ok);
+    const unsigned conm = __ballot_sync(0xffffu, ok && tid < KPIX - 1 && nxt == pix + 1);
+    if (tid == 0) {
+        unsigned fl = 0;
+        for (int kb = 0; kb < KB / 8; ++kb) {
+            const int pa = (8 * kb) / 3, pz = (8 * kb + 7) / 3;
+            const unsigned mo = ((2u << pz) - 1u) & ~((1u << pa) - 1u);  // pixels pa .. pz
+            const unsigned mc = ((1u << pz) - 1u) & ~((1u << pa) - 1u);  // steps pa -> pa + 1 .. pz - 1 -> pz
+            if ((okm & mo) == mo && (conm & mc) == mc) fl |= 1u << kb;
+        }
+        *bFlag = fl;
+    }
 }
 
 // In-frame geometry of one (pixel, sample) pair, as in the FP32 kernel: returns
@@ -198,8 +237,13 @@ __device__ __forceinline__ float rcp_approx(float x) {
 
 }  // namespace
 
+// `rows` is the realization stack seen as a 3-D tensor of 16-bit values: element
+// (c, y, q) = realization 8 q + c of row y = 3 p + m (map m of pixel p), with a box of
+// 8 x 8 x R/8 whose shared-memory image [q][8 rows][8] is the B operand's core matrices
+// (k-block, q) at 128-byte strides.
 template <int F16>
-__global__ void __launch_bounds__(MT, 1) k_mr(const __grid_constant__ LaunchParams P) {
+__global__ void __launch_bounds__(MT, 1) k_mr(const __grid_constant__ LaunchParams P,
+                                              const __grid_constant__ CUtensorMap rows) {
     __shared__ double sTh[MS], sPh[MS], sPx[MS], sPy[MS], sPz[MS];
     __shared__ float4 sA[MS], sB[MS];
     __shared__ float sBf[MS];
@@ -213,8 +257,10 @@ __global__ void __launch_bounds__(MT, 1) k_mr(const __grid_constant__ LaunchPara
     // pixel data of the current and the next batch
     __shared__ int bRi[2][KPIX], bJw[2][KPIX], bOk[2][KPIX];
     __shared__ long long bPix[2][KPIX];
+    __shared__ unsigned bFlag[2];  // core matrices of the batch loaded by TMA (bit kb)
     __shared__ float bSa[2][KPIX], bCa[2][KPIX];
-    __shared__ __align__(8) unsigned long long mbar[2];
+    __shared__ __align__(8) unsigned long long mbar[2];  // MMAs of buffer b done
+    __shared__ __align__(8) unsigned long long lbar[2];  // TMA loads into buffer b done
     __shared__ unsigned tmem_base;
     __shared__ int failed;
     extern __shared__ unsigned char mr_dyn_raw[];
@@ -241,6 +287,9 @@ __global__ void __launch_bounds__(MT, 1) k_mr(const __grid_constant__ LaunchPara
     if (tid == 0) {
         mbar_init(mbar + 0);
         mbar_init(mbar + 1);
+        mbar_init(lbar + 0);
+        mbar_init(lbar + 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         failed = 0;
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -249,6 +298,8 @@ __global__ void __launch_bounds__(MT, 1) k_mr(const __grid_constant__ LaunchPara
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const unsigned tmem = tmem_base;
     unsigned phase[2] = {0u, 0u};
+    unsigned lphase[2] = {0u, 0u};  // load mbarrier parities (thread 0 waits on them)
+    bool lfail = false;             // thread 0: a wait for loads timed out (shared flag set before a barrier)
     bool pend[2] = {false, false};
 
     // wait for the MMAs that read buffer b (all threads); false after a timeout
@@ -437,7 +488,7 @@ __global__ void __launch_bounds__(MT, 1) k_mr(const __grid_constant__ LaunchPara
             // the first batch's pixel data; each batch then prepares the next one's
             if (tid < KPIX && total > 0)
                 batch_pixel(0, tid, nr, total, sPref, sJlo, sRc, sJref, sDph, sAref, sFirst, bRi[0], bJw[0], bOk[0],
-                            bSa[0], bCa[0], bPix[0]);
+                            bSa[0], bCa[0], bPix[0], bFlag + 0);
             __syncthreads();
             int fb = 0;  // batch within the chunk
             for (int f0 = 0; f0 < total && !failed; f0 += KPIX, ++batch, ++fb) {
@@ -446,16 +497,29 @@ __global__ void __launch_bounds__(MT, 1) k_mr(const __grid_constant__ LaunchPara
                 unsigned char* bAh = bB + B_BYTES;
                 unsigned char* bAl = bAh + A_BYTES;
                 // the MMAs of two batches ago read this buffer
-                if (!drain(buf)) atomicOr(&failed, 1);
-                // 4. realization rows into the B operand: 16-byte chunk (k = 3 p + m, r = 8 q .. 8 q + 7)
+                if (!drain(buf) || lfail) atomicOr(&failed, 1);
+                // 4. realization rows into the B operand, core matrix (kb, q) = rows k = 8 kb .. 8 kb + 7
+                //    (k = 3 p + m) x realizations 8 q .. 8 q + 7: by TMA (warp 0) when its rows are
+                //    consecutive in the stack, else as 16-byte chunks (all threads) or zeros
                 {
                     const int qn = nreal / 8;
-                    for (int c = tid; c < KB * qn; c += MT) {
-                        const int k = c / qn, q = c % qn;
-                        const int p = k / 3, m = k % 3;
-                        unsigned char* dst = bB + (k >> 3) * b_lbo + q * B_SBO + (k & 7) * 16;
-                        if (bOk[pb][p]) cp_async16(dst, sky16 + (bPix[pb][p] * 3 + m) * (long long)nreal + 8 * q);
-                        else *(uint4*)dst = make_uint4(0u, 0u, 0u, 0u);
+                    const unsigned fl = bFlag[pb];
+                    if (warp == 0) {
+                        if (lane == 0) mbar_expect_tx(lbar + buf, (unsigned)(__popc(fl) * qn * 128));
+                        __syncwarp();
+                        const int kb = lane, k0 = 8 * lane;
+                        if (kb < KB / 8 && ((fl >> kb) & 1u))
+                            tma_tile3(bB + kb * b_lbo, &rows, (int)(bPix[pb][k0 / 3] * 3 + k0 % 3), lbar + buf);
+                    }
+                    if (fl != (1u << (KB / 8)) - 1u) {
+                        for (int c = tid; c < KB * qn; c += MT) {
+                            const int k = c / qn, q = c % qn;
+                            if ((fl >> (k >> 3)) & 1u) continue;
+                            const int p = k / 3, m = k % 3;
+                            unsigned char* dst = bB + (k >> 3) * b_lbo + q * B_SBO + (k & 7) * 16;
+                            if (bOk[pb][p]) cp_async16(dst, sky16 + (bPix[pb][p] * 3 + m) * (long long)nreal + 8 * q);
+                            else *(uint4*)dst = make_uint4(0u, 0u, 0u, 0u);
+                        }
                     }
                     asm volatile("cp.async.commit_group;" ::: "memory");
                 }
@@ -506,21 +570,34 @@ __global__ void __launch_bounds__(MT, 1) k_mr(const __grid_constant__ LaunchPara
                 }
                 if (tid < KPIX && f0 + KPIX < total)
                     batch_pixel(f0 + KPIX, tid, nr, total, sPref, sJlo, sRc, sJref, sDph, sAref, sFirst, bRi[pb ^ 1],
-                                bJw[pb ^ 1], bOk[pb ^ 1], bSa[pb ^ 1], bCa[pb ^ 1], bPix[pb ^ 1]);
+                                bJw[pb ^ 1], bOk[pb ^ 1], bSa[pb ^ 1], bCa[pb ^ 1], bPix[pb ^ 1], bFlag + (pb ^ 1));
                 asm volatile("cp.async.wait_group 0;" ::: "memory");
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 __syncthreads();
-                if (failed) break;
-                // 6. one thread issues the batch's MMAs: D[t][r] += sum_k (W_hi + W_lo)[t][k] S[k][r]
+                if (failed) {
+                    // leave no TMA load in flight: thread 0 waits (bounded) for this batch's loads
+                    if (tid == 0) mbar_wait(lbar + buf, lphase[buf]);
+                    break;
+                }
+                // 6. one thread waits for the batch's loads and issues its MMAs:
+                //    D[t][r] += sum_k (W_hi + W_lo)[t][k] S[k][r]; the commit is made even when the
+                //    loads timed out (no MMAs then), so the MMA mbarrier phases stay in step
                 if (tid == 0) {
-                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const bool loaded = mbar_wait(lbar + buf, lphase[buf]);
+                    lphase[buf] ^= 1u;
+                    if (!loaded) {
+                        atomicOr(P.err, 2);
+                        lfail = true;
+                    } else {
+                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-                    for (int ks = 0; ks < KB / 16; ++ks) {
-                        const unsigned long long bd = smem_desc(smem_u32(bB + ks * 2 * b_lbo), b_lbo, B_SBO);
-                        const unsigned long long ah = smem_desc(smem_u32(bAh + ks * 2 * A_LBO), A_LBO, A_SBO);
-                        const unsigned long long al = smem_desc(smem_u32(bAl + ks * 2 * A_LBO), A_LBO, A_SBO);
-                        mma_f16(tmem, ah, bd, idesc, (batch > 0 || ks > 0) ? 1u : 0u);
-                        mma_f16(tmem, al, bd, idesc, 1u);
+                        for (int ks = 0; ks < KB / 16; ++ks) {
+                            const unsigned long long bd = smem_desc(smem_u32(bB + ks * 2 * b_lbo), b_lbo, B_SBO);
+                            const unsigned long long ah = smem_desc(smem_u32(bAh + ks * 2 * A_LBO), A_LBO, A_SBO);
+                            const unsigned long long al = smem_desc(smem_u32(bAl + ks * 2 * A_LBO), A_LBO, A_SBO);
+                            mma_f16(tmem, ah, bd, idesc, (batch > 0 || ks > 0) ? 1u : 0u);
+                            mma_f16(tmem, al, bd, idesc, 1u);
+                        }
                     }
                     mma_commit(mbar + buf);
                 }
@@ -530,7 +607,7 @@ __global__ void __launch_bounds__(MT, 1) k_mr(const __grid_constant__ LaunchPara
 
         // 7. epilogue: wait for every MMA of the tile, read D back, d = scale * D (NaN for invalid samples)
         const bool ok0 = drain(0), ok1 = drain(1);
-        if (!ok0 || !ok1) {
+        if (!ok0 || !ok1 || lfail) {
             atomicOr(P.err, 2);
             failed = 1;
         }
@@ -577,18 +654,52 @@ __global__ void __launch_bounds__(MT, 1) k_mr(const __grid_constant__ LaunchPara
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
 }
 
+namespace {
+
+// cuTensorMapEncodeTiled, looked up once through the runtime (no link to the driver library).
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encode_tiled() {
+    static EncodeTiled fn = [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            f = nullptr;
+        return (EncodeTiled)f;
+    }();
+    return fn;
+}
+
+}  // namespace
+
 cudaError_t launch_mr(const LaunchParams& p, int f16, cudaStream_t s) {
     if (p.total_tiles <= 0) return cudaSuccess;
+    // the stack [3 Npix][R] of 16-bit values as (8 realizations, rows, R / 8 groups): innermost
+    // box extent 16 bytes, every box starts at column 0 of its group (16-byte aligned)
+    const EncodeTiled encode = encode_tiled();
+    if (!encode || 3 * p.npix >= INT_MAX || p.n_real % 8 != 0 || p.n_real > 256) return cudaErrorInvalidValue;
+    CUtensorMap rows;
+    const cuuint64_t dims[3] = {8, (cuuint64_t)(3 * p.npix), (cuuint64_t)(p.n_real / 8)};
+    const cuuint64_t strides[2] = {(cuuint64_t)p.n_real * 2, 16};
+    const cuuint32_t box[3] = {8, 8, (cuuint32_t)(p.n_real / 8)}, estr[3] = {1, 1, 1};
+    if (encode(&rows, CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, const_cast<void*>(p.sky), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
     const unsigned grid = (unsigned)min(p.total_tiles, (long long)INT_MAX);
     cudaError_t e;
     if (f16) {
         e = cudaFuncSetAttribute(k_mr<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, MR_DYN_SMEM);
         if (e != cudaSuccess) return e;
-        k_mr<1><<<grid, MT, MR_DYN_SMEM, s>>>(p);
+        k_mr<1><<<grid, MT, MR_DYN_SMEM, s>>>(p, rows);
     } else {
         e = cudaFuncSetAttribute(k_mr<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, MR_DYN_SMEM);
         if (e != cudaSuccess) return e;
-        k_mr<0><<<grid, MT, MR_DYN_SMEM, s>>>(p);
+        k_mr<0><<<grid, MT, MR_DYN_SMEM, s>>>(p, rows);
     }
     return cudaGetLastError();
 }
