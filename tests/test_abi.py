@@ -52,6 +52,27 @@ def test_create_rejects_bad_arguments_before_touching_the_device(lib):
         assert lib.pisco_last_error(None)
 
 
+def test_multirealization_options_are_checked_before_touching_the_device(lib):
+    """Realization count, stack dtype and the nside bound of the tensor-core path (its TMA row
+    coordinates, 3 Npix rows, are 32-bit)."""
+    handle = ctypes.c_void_p()
+    det = (pisco.pisco_detector * 1)(pisco.pisco_detector(0.0, 0.0, 1.0))
+    cases = [
+        (8, pisco.PISCO_BF16_MR, pisco.PISCO_DTYPE_BF16, 48),    # not a multiple of 32
+        (8, pisco.PISCO_BF16_MR, pisco.PISCO_DTYPE_BF16, 288),   # above 256
+        (8, pisco.PISCO_BF16_MR, pisco.PISCO_DTYPE_F16, 64),     # FP16 stack on a BF16 plan
+        (8, pisco.PISCO_FP16_MR, pisco.PISCO_DTYPE_F32, 64),     # FP32 sky on an FP16 plan
+        (7724, pisco.PISCO_BF16_MR, pisco.PISCO_DTYPE_BF16, 32),  # 36 nside^2 >= 2^31
+    ]
+    for nside, precision, dtype, n_real in cases:
+        opt = pisco.pisco_options(precision, 0, 0, 0, n_real)
+        st = lib.pisco_plan_create(ctypes.byref(handle), nside, 0.1, ctypes.c_void_p(16), dtype, 1, det, 11,
+                                   ctypes.c_void_p(16), None, ctypes.byref(opt), None)
+        assert st == pisco.PISCO_EINVAL, (nside, precision, dtype, n_real)
+        assert handle.value is None
+        assert lib.pisco_last_error(None)
+
+
 def test_calls_on_a_null_plan_are_rejected(lib):
     assert lib.pisco_convolve(None, 0, 0, None, None, None, None, None) == pisco.PISCO_EINVAL
     assert lib.pisco_adjoint(None, 0, 0, None, None, None, None, None, 0, None) == pisco.PISCO_EINVAL
