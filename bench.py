@@ -690,6 +690,8 @@ def main():
     rank, world, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, rank, world)
+        if world > 1:
+            torch.distributed.destroy_process_group()
         return
     if args.workload != "single":
         torch.cuda.set_device(local)
