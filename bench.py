@@ -53,6 +53,19 @@ WORKLOAD = dict(workload="single-detector FP32: nside 512 sky, 1.5 deg beam + 1%
 FLOPS_PER_PAIR = 78
 # FP32 peak of the GPU from unit counts: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+def measured_peaks(path=os.path.join(ROOT, "MEASURED_PEAKS.json")):
+    """(HBM GB/s, dense BF16 TFLOP/s burst, source): the copy bandwidth and cuBLAS BF16 rate
+    measured on this machine's GPUs when the file is there, else the fallback figures."""
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), float(d["bf16_tflops"]), "measured"
+    except (OSError, ValueError, KeyError, TypeError):
+        return 6800.0, 1900.0, "fallback"
+
+
+HBM_GBS, BF16_TFLOPS, PEAK_SOURCE = measured_peaks()
+
 # DRAM bytes (read + write) of one forward launch on the default single-detector workload
 # (1e7 samples, 16-sample tiles, 1 pixel per thread, 64-byte cells) from one ncu capture of
 # dram__bytes_read.sum + dram__bytes_write.sum (1 pass, full-size launch): 486.63 MB read,
@@ -407,10 +420,10 @@ def run_multireal(args, dev):
         "fp32_per_realization": {"value": fp32_rate, "unit": UNIT, "realizations_timed": 1,
                                  "note": "FP32 path, one realization per pass, divided by 256",
                                  "speedup_of_bf16": (n / (ms / 1e3)) / fp32_rate},
-        "roofline": {"bound": "tensor", "achieved": achieved, "peak": 1927.2, "unit": "TFLOP/s",
-                     "frac": achieved / 1927.2, "traffic": None,
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": BF16_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / BF16_TFLOPS, "traffic": None, "peak_source": PEAK_SOURCE,
                      "note": "algorithmic 2*3*pairs*R flops (the hi/lo weight split doubles the issued MMAs); "
-                             "bf16 peak of measured"},
+                             "dense BF16 burst peak"},
         "gpu_launches": args.steps, "clocks": clk}))
 
 
@@ -800,7 +813,7 @@ def main():
                          "traffic_note": "ncu DRAM bytes read + written per forward launch",
                          "kernel": f"pisco::k_fast<{tuned[0]}, {tuned[1]}, cells, forward>",
                          "peak_note": "FP32 from unit counts: 152 SM x 128 lanes x 2 x 2070 MHz",
-                         "hbm_frac_of_measured": (28 * n / (ms / 1e3)) / 6758.2e9},
+                         "hbm_frac": (28 * n / (ms / 1e3)) / (HBM_GBS * 1e9), "hbm_peak_source": PEAK_SOURCE},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 24 * n, "d2h_bytes_per_step": 4 * n},
             "plain_fp64_gpu": {"value": plain_rate * world, "unit": UNIT, "samples_timed": n_plain,
                                "speedup_of_fp32": value / (plain_rate * world),

@@ -35,3 +35,12 @@ def test_forward_traffic_is_reported_only_for_the_captured_launch_shape():
     assert bench.FORWARD_TRAFFIC_BYTES.get((10_000_000, 16, 1)) == 486.63e6 + 47.03e6
     assert bench.FORWARD_TRAFFIC_BYTES.get((500_000, 16, 1)) is None
     assert bench.FORWARD_TRAFFIC_BYTES.get((10_000_000, 32, 1)) is None
+
+
+def test_peaks_come_from_the_measured_file_else_the_fallback(tmp_path):
+    f = tmp_path / "peaks.json"
+    f.write_text('{"hbm_gbs": 6779.7, "bf16_tflops": 1944.1, "bf16_tflops_sustained": 1726.7}')
+    assert bench.measured_peaks(str(f)) == (6779.7, 1944.1, "measured")
+    assert bench.measured_peaks(str(tmp_path / "absent.json")) == (6800.0, 1900.0, "fallback")
+    f.write_text('{"hbm_gbs": null}')
+    assert bench.measured_peaks(str(f))[2] == "fallback"
