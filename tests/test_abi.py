@@ -91,3 +91,24 @@ def test_healpix_beam_resampling_rejects_bad_arguments_before_touching_the_devic
         st = lib.pisco_beam_grids_from_healpix(nside_b, n_maps, p, radius, grid_n, p, None)
         assert st == pisco.PISCO_EINVAL
         assert lib.pisco_last_error(None)
+
+
+def test_map_making_rejects_bad_arguments_before_touching_the_device(lib):
+    p = ctypes.c_void_p(16)
+    ok_det = pisco.pisco_detector(0.0, 0.0, 1.0)
+    nan_det = pisco.pisco_detector(float("nan"), 0.0, 1.0)
+    for nside in (0, 8193):
+        assert lib.pisco_ang2pix(nside, 1, p, p, p, None) == pisco.PISCO_EINVAL
+        assert lib.pisco_map_solve(nside, p, 0.0, p, None) == pisco.PISCO_EINVAL
+    assert lib.pisco_ang2pix(8, -1, p, p, p, None) == pisco.PISCO_EINVAL
+    assert lib.pisco_ang2pix(8, 0, None, None, None, None) == pisco.PISCO_OK  # nothing to do
+    cases = [dict(n=-1), dict(det=None), dict(det=nan_det), dict(dtype=pisco.PISCO_DTYPE_BF16), dict(nside=0)]
+    for c in cases:
+        det = c.get("det", ok_det)
+        st = lib.pisco_map_accumulate(c.get("nside", 8), c.get("n", 4), p, p, p,
+                                      None if det is None else ctypes.byref(det), p,
+                                      c.get("dtype", pisco.PISCO_DTYPE_F32), p, 0, None)
+        assert st == pisco.PISCO_EINVAL, c
+        assert lib.pisco_last_error(None)
+    for rcond in (-0.1, 1.5, float("nan")):
+        assert lib.pisco_map_solve(8, p, rcond, p, None) == pisco.PISCO_EINVAL
