@@ -82,6 +82,17 @@ def test_calls_on_a_null_plan_are_rejected(lib):
     assert lib.pisco_plan_autotune(None, 0, 10, None, None, None, None, 1, None, None, None, None) == pisco.PISCO_EINVAL
     z = (ctypes.c_double * 2)(0.0, 1.0)
     assert lib.pisco_convolve_psb(None, 0, 0, None, None, None, 2, z, None, None) == pisco.PISCO_EINVAL
+    off = (ctypes.c_int64 * 2)(0, 4)
+    assert lib.pisco_convolve_batched(None, 1, off, None, None, None, None, None) == pisco.PISCO_EINVAL
+    assert lib.pisco_beam_grid_adjoint(None, 0, 0, None, None, None, None, None, 0, None) == pisco.PISCO_EINVAL
+    assert lib.pisco_beam_grid_adjoint_static(None, 0, 0, None, None, None, None, None, 0,
+                                              None) == pisco.PISCO_EINVAL
+    assert lib.pisco_adjoint_sky_beam(None, 0, 0, None, None, None, None, None, None, 0, None) == pisco.PISCO_EINVAL
+    assert lib.pisco_omega_adjoint(None, 0, 0, None, None, None, None) == pisco.PISCO_EINVAL
+    assert lib.pisco_update_beams(None, None, None, None) == pisco.PISCO_EINVAL
+    assert lib.pisco_convolve_host(None, 0, 0, None, None, None, None) == pisco.PISCO_EINVAL
+    om, sc = ctypes.c_double(), ctypes.c_double()
+    assert lib.pisco_plan_omega(None, 0, ctypes.byref(om), ctypes.byref(sc)) == pisco.PISCO_EINVAL
 
 
 def test_healpix_beam_resampling_rejects_bad_arguments_before_touching_the_device(lib):
