@@ -54,7 +54,7 @@ typedef enum pisco_status {
     PISCO_EINVAL = 1,        /* bad argument; nothing was enqueued */
     PISCO_ENOMEM = 2,        /* device or host allocation failed */
     PISCO_ECUDA = 3,         /* a CUDA runtime call failed */
-    PISCO_ETIMEOUT = 4,      /* reserved: a bounded device wait gave up */
+    PISCO_ETIMEOUT = 4,      /* a bounded device wait gave up (reported by pisco_sync_status) */
     PISCO_EUNSUPPORTED = 5,  /* valid request this build does not implement */
     PISCO_EDEVICE = 6        /* a kernel recorded an invariant violation */
 } pisco_status;
@@ -388,7 +388,10 @@ pisco_status pisco_plan_autotune(pisco_plan* plan, int det, int64_t n,
                                  int* pixels_per_thread, float* best_ms, void* stream);
 
 /* Synchronise the plan's work on `stream` and report any error a kernel
- * recorded since the last call (PISCO_EDEVICE), clearing it. */
+ * recorded since the last call, clearing it: PISCO_ETIMEOUT when a bounded
+ * device wait gave up (flag 2: the multi-realization kernel waits about two
+ * seconds at most for its MMAs and its TMA loads, then stops issuing, frees
+ * its tensor memory and returns), PISCO_EDEVICE for any other flag. */
 pisco_status pisco_sync_status(pisco_plan* plan, void* stream);
 
 #ifdef __cplusplus

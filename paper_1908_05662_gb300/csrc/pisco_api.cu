@@ -612,8 +612,9 @@ extern "C" pisco_status pisco_sync_status(pisco_plan* plan, void* stream) {
     PISCO_CUDA(plan, cudaMemcpy(&h, plan->d_err, sizeof(int), cudaMemcpyDeviceToHost));
     if (h != 0) {
         PISCO_CUDA(plan, cudaMemset(plan->d_err, 0, sizeof(int)));
-        set_error(plan, "a kernel recorded error flags 0x%x", h);
-        return PISCO_EDEVICE;
+        set_error(plan, "a kernel recorded error flags 0x%x%s", h,
+                  (h & 2) ? " (a bounded wait on an mbarrier gave up)" : "");
+        return (h & 2) ? PISCO_ETIMEOUT : PISCO_EDEVICE;
     }
     return PISCO_OK;
 }
