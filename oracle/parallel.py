@@ -54,21 +54,25 @@ def tod_sampled(nside, radius, sky, grids, det, omega, theta0, phi0, psi0, proce
         env = dict(os.environ, **_ONE_THREAD)
         env["PYTHONPATH"] = _ROOT + os.pathsep + env.get("PYTHONPATH", "")
         procs = []
-        for j in range(processes):
-            a = n * j // processes
-            b = min(n * (j + 1) // processes, a + limit)
-            procs.append(subprocess.Popen([sys.executable, "-m", "oracle.parallel", tmp, str(j), str(a), str(b)],
-                                          cwd=_ROOT, env=env))
-        # start the loops together once every worker has loaded its inputs
-        deadline = time.time() + 600.0
-        while not all(os.path.exists(os.path.join(tmp, f"ready{j}")) for j in range(processes)):
-            if time.time() > deadline or any(p.poll() not in (None, 0) for p in procs):
-                for p in procs:
+        try:
+            for j in range(processes):
+                a = n * j // processes
+                b = min(n * (j + 1) // processes, a + limit)
+                procs.append(subprocess.Popen(
+                    [sys.executable, "-m", "oracle.parallel", tmp, str(j), str(a), str(b)], cwd=_ROOT, env=env))
+            # start the loops together once every worker has loaded its inputs
+            deadline = time.time() + 600.0
+            while not all(os.path.exists(os.path.join(tmp, f"ready{j}")) for j in range(processes)):
+                if time.time() > deadline or any(p.poll() not in (None, 0) for p in procs):
+                    raise RuntimeError("oracle workers did not start")
+                time.sleep(0.002)
+            open(os.path.join(tmp, "go"), "w").close()
+            codes = [p.wait() for p in procs]
+        finally:
+            for p in procs:  # none is left running when this call ends, however it ends
+                if p.poll() is None:
                     p.kill()
-                raise RuntimeError("oracle workers did not start")
-            time.sleep(0.002)
-        open(os.path.join(tmp, "go"), "w").close()
-        codes = [p.wait() for p in procs]
+                    p.wait()
         if any(codes):
             raise RuntimeError(f"oracle workers failed with exit codes {codes}")
         idx, vals, t0, t1 = [], [], [], []
