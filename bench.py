@@ -83,8 +83,9 @@ def parse():
     ap.add_argument("--samples", type=int, default=WORKLOAD["n_samples"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline leg")
     ap.add_argument("--workload", default="single",
-                    choices=["single", "focalplane", "multireal", "table1", "psb", "sec61", "grad"],
-                    help="single: the default single-detector line; the others measure the focal-plane, "
+                    choices=["single", "c1", "focalplane", "multireal", "table1", "psb", "sec61", "grad"],
+                    help="single: the default single-detector line; the others measure the plain-FP64 baseline "
+                         "configuration (c1), the focal-plane, "
                          "multi-realization, Table 1 replica, PSB-pair (shared geometry) and Sec. 6.1 "
                          "(TOD then binned maps) configurations, and grad: the differentiation configuration")
     return ap.parse_args()
@@ -254,6 +255,81 @@ def _event_time(fn, steps, warmup, stream):
     e1.record(stream)
     torch.cuda.synchronize()
     return e0.elapsed_time(e1) / steps
+
+
+def run_c1(args, dev):
+    """The plain-FP64 baseline configuration: nside 128 sky, elliptical Gaussian beam (FWHM 1.5 deg,
+    ellipticity 0.05) as 6 maps on a 101^2 grid of radius 5 deg, 1e5 samples of a constant-elevation
+    raster with psi stepping uniformly over [0, 2 pi).  One step = one pisco_convolve over all samples
+    (FP32 path, tile shape from the autotuner); the plain FP64 path runs the whole scan too, the
+    packed-cell fetch beside it, and the oracle on a bounded sample of the scan on every host core."""
+    nside, r, n_grid = 128, math.radians(5.0), 101
+    n = 100_000 if args.samples == WORKLOAD["n_samples"] else args.samples
+    sky = cached_sky(nside, 1, dev)
+    grids = sy.gaussian_beam_maps(n_grid, r, 1.5, ellipticity=0.05)
+    g = torch.as_tensor(grids, device=dev)[None].contiguous()
+    th, ph, ps = (torch.as_tensor(a, device=dev).contiguous() for a in sy.raster_scan(n, rows=100))
+    det = (0.0, 0.0, 1.0)
+    stream = torch.cuda.current_stream()
+    plan = pisco.Plan(nside, r, sky, [det], g)
+    tuned = plan.autotune(th, ph, ps, reps=3)
+    pairs = int(plan.disc_count(th, ph).to(torch.int64).sum().item())
+    tod = torch.empty(n, dtype=torch.float32, device=dev)
+    with ClockSampler(torch.cuda.current_device()) as clocks:
+        ms = _event_time(lambda: plan.convolve(th, ph, ps, out=tod), args.steps, args.warmup, stream)
+    plan.sync_status()
+    legs = {}
+    for name, fetch in (("packed_cells", pisco.PISCO_FETCH_PACKED),):
+        with pisco.Plan(nside, r, sky, [det], g, beam_fetch=fetch, tile_samples=tuned[0],
+                        pixels_per_thread=tuned[1]) as other:
+            t_o = torch.empty(n, dtype=torch.float32, device=dev)
+            ms_o = _event_time(lambda: other.convolve(th, ph, ps, out=t_o), args.steps, args.warmup, stream)
+            other.sync_status()
+        legs[name] = (ms_o, t_o)
+    with pisco.Plan(nside, r, sky, [det], g, precision=pisco.PISCO_FP64_PLAIN) as plain:
+        tod64 = torch.empty(n, dtype=torch.float64, device=dev)
+        ms_plain = _event_time(lambda: plain.convolve(th, ph, ps, out=tod64), 2, 1, stream)
+        plain.sync_status()
+    fp32_vs_64 = ((tod.double() - tod64).abs().max() / tod64.abs().max()).item()
+    out = {"metric": "TOD samples/s (plain-FP64 baseline configuration: nside 128, R 5 deg, 101^2 grid)",
+           "value": n / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic",
+           "config": {"workload": "nside 128 sky, FWHM 1.5 deg e 0.05 beam, 101^2 grid of radius 5 deg, "
+                                  "1e5 raster samples", "samples": n, "pairs_per_step": pairs,
+                      "tile_samples": tuned[0], "pixels_per_thread": tuned[1],
+                      "l2": "inputs (2.4 MB pointing, 3 MB sky, 0.6 MB beam) are L2-resident"},
+           "plain_fp64_gpu": {"value": n / (ms_plain / 1e3), "unit": UNIT, "ms_per_step": ms_plain,
+                              "samples_timed": n, "speedup_of_fp32": ms_plain / ms,
+                              "fp32_vs_fp64_normwise": fp32_vs_64},
+           "roofline": {"bound": "alu", "achieved": FLOPS_PER_PAIR * pairs / (ms / 1e3) / 1e12,
+                        "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                        "frac": FLOPS_PER_PAIR * pairs / (ms / 1e3) / 1e12 / FP32_PEAK_TFLOPS, "traffic": None},
+           "gpu_launches": args.steps, "clocks": clocks.summary()}
+    for name, (ms_o, t_o) in legs.items():
+        out[name] = {"value": n / (ms_o / 1e3), "unit": UNIT, "ms_per_step": ms_o,
+                     "vs_default_normwise": ((t_o.double() - tod.double()).abs().max() /
+                                             tod.double().abs().max()).item()}
+    if not args.no_cpu:
+        thn, phn, psn = th.cpu().numpy(), ph.cpu().numpy(), ps.cpu().numpy()
+        from oracle import beam as ob
+        from oracle import parallel as op
+        g64 = grids.astype(np.float64)
+        idx, ref, span, cores = op.tod_sampled(nside, r, sky.cpu().numpy(), g64, det, ob.omega_tilde(g64[0], r),
+                                               thn, phn, psn, budget_s=10.0)
+        sel = torch.as_tensor(idx, device=dev)
+        out["cpu_baseline"] = {"value": len(idx) / span, "unit": UNIT, "cores": cores, "kind": "oracle",
+                               "sample": f"{len(idx)} samples: {cores} single-threaded worker processes, "
+                                         "each ~10 s on consecutive samples from its own offset"}
+        out["err_vs_oracle_normwise"] = float(np.max(np.abs(tod[sel].double().cpu().numpy() - ref)) /
+                                              np.max(np.abs(ref)))
+        out["plain_fp64_gpu"]["err_vs_oracle_normwise"] = float(
+            np.max(np.abs(tod64[sel].cpu().numpy() - ref)) / np.max(np.abs(ref)))
+        for name, (_, t_o) in legs.items():
+            out[name]["err_vs_oracle_normwise"] = float(np.max(np.abs(t_o[sel].double().cpu().numpy() - ref)) /
+                                                        np.max(np.abs(ref)))
+    plan.close()
+    print(json.dumps(out))
 
 
 def run_focalplane(args, dev):
@@ -708,7 +784,7 @@ def main():
         return
     if args.workload != "single":
         torch.cuda.set_device(local)
-        {"focalplane": run_focalplane, "multireal": run_multireal, "table1": run_table1, "psb": run_psb,
+        {"c1": run_c1, "focalplane": run_focalplane, "multireal": run_multireal, "table1": run_table1, "psb": run_psb,
          "sec61": run_sec61, "grad": run_grad}[args.workload](
             args, torch.device("cuda", local))
         return

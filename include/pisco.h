@@ -387,6 +387,18 @@ pisco_status pisco_plan_autotune(pisco_plan* plan, int det, int64_t n,
                                  void* tod_scratch, int reps, int* tile_samples,
                                  int* pixels_per_thread, float* best_ms, void* stream);
 
+/*
+ * pisco_inject_mr_stall -- test hook for the failure detection of the
+ * multi-realization kernel (no counterpart in the paper).  The next launch of
+ * pisco_convolve or pisco_convolve_batched on this (PISCO_BF16_MR or
+ * PISCO_FP16_MR) plan first waits `cycles` SM clocks on an mbarrier that
+ * nothing arrives on, before it issues any copy or MMA: the wait gives up,
+ * the kernel records error bit 2, writes no TOD, releases its tensor memory
+ * and returns, and pisco_sync_status reports PISCO_ETIMEOUT.  Later launches
+ * run normally.  cycles in [1, 1e10]; PISCO_EUNSUPPORTED for other plans.
+ */
+pisco_status pisco_inject_mr_stall(pisco_plan* plan, int64_t cycles);
+
 /* Synchronise the plan's work on `stream` and report any error a kernel
  * recorded since the last call, clearing it: PISCO_ETIMEOUT when a bounded
  * device wait gave up (flag 2: the multi-realization kernel waits about two

@@ -407,6 +407,8 @@ pisco_status pisco::run(pisco_plan* plan, int mode, int d0, int nd, const int64_
                 set_error(plan, "multi-realization plans support pisco_convolve and pisco_convolve_batched only");
                 return PISCO_EUNSUPPORTED;
             }
+            L.stall_cycles = plan->mr_stall;
+            plan->mr_stall = 0;
             e = launch_mr(L, plan->precision == PISCO_FP16_MR, s);
         } else if (plan->precision == PISCO_FP64_PLAIN) e = launch_plain(L, mode, s);
         else if (plan->beam_fetch == PISCO_FETCH_CELLS)
@@ -602,6 +604,20 @@ extern "C" pisco_status pisco_convolve_host(pisco_plan* plan, int det, int64_t n
     }
     PISCO_CUDA(plan, cudaStreamSynchronize(plan->hs[0]));
     PISCO_CUDA(plan, cudaStreamSynchronize(plan->hs[1]));
+    return PISCO_OK;
+}
+
+extern "C" pisco_status pisco_inject_mr_stall(pisco_plan* plan, int64_t cycles) {
+    if (!plan) return PISCO_EINVAL;
+    if (plan->precision != PISCO_BF16_MR && plan->precision != PISCO_FP16_MR) {
+        set_error(plan, "pisco_inject_mr_stall needs a multi-realization plan");
+        return PISCO_EUNSUPPORTED;
+    }
+    if (cycles < 1 || cycles > 10000000000LL) {
+        set_error(plan, "stall of %lld cycles outside [1, 1e10]", (long long)cycles);
+        return PISCO_EINVAL;
+    }
+    plan->mr_stall = cycles;
     return PISCO_OK;
 }
 

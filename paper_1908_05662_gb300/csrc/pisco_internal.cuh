@@ -70,6 +70,9 @@ struct LaunchParams {
     int n_zeta;            // shared-geometry pass: number of polarisation angles
     long long out_stride;  // shared-geometry pass: elements between the TODs of two angles
     float psb_c2z[kMaxPsb], psb_s2z[kMaxPsb];  // cos, sin of 2 (zeta_k - zeta of the plan's detector)
+    long long wait_limit;    // multi-realization kernel: SM clocks a wait on an mbarrier may take (0: ~2 s)
+    long long stall_cycles;  // multi-realization kernel, test hook: > 0 makes it wait this long, before it
+                             // issues any copy or MMA, on an mbarrier nothing arrives on (a timeout)
     int ndet;
     long long total_tiles;
     DetEntry det[kMaxDetPerLaunch];
@@ -107,6 +110,7 @@ struct pisco_plan {
     void* d_stage[2];
     size_t stage_bytes;
     void* d_gscratch;  // beam-grid adjoint: folded gradient [3][N][N] (float or double)
+    long long mr_stall;  // test hook: stall cycles for the next multi-realization launch (0: none)
     char msg[512];
 };
 

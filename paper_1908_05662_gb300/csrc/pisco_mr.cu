@@ -5,36 +5,57 @@
 // factored out):
 //     d_r(t) = scale * sum_k sum_{m = I,Q,U} W[t][k][m] S_r[k][m],
 //     W[t][k] = (A, (Bq' re + 2 Cu' im2) / sin^2 theta_k, (Cu' re - 2 Bq' im2) / sin^2 theta_k),
-// the pair weights of the FP32 kernel.  One CTA owns 128 consecutive samples
-// of one detector, the M dimension of the MMA; the realizations are N (up to
-// 256), so the whole 128 x R accumulator lives in tensor memory (TMEM) for
-// the tile.  The CTA traverses the union of the 128 discs ring by ring (the
-// ring-ordered disc query of the FP32 kernel) and, per batch of 16 union
-// pixels (K = 48: pixel x I, Q, U):
-//   1. copies the realization rows [pixel][I,Q,U][R] (16-bit) straight into
-//      the B operand's MN-major core-matrix layout (8 k-rows x 16 bytes per
-//      core matrix, no swizzle): a core matrix whose 8 rows are consecutive
-//      in the stack (pixels of one ring run) comes by TMA: one 3-D tile load
-//      per 8-row block fills its core matrices for all realizations (8 rows x
-//      R realizations, completing on the buffer's load mbarrier); blocks with
-//      a run boundary inside, or in the batch's tail, are 16-byte asynchronous
-//      copies and zeros;
-//   2. computes the 128 x 16 pair weights in FP32 (zero outside a sample's
-//      disc) and splits each into two 16-bit parts, W = W_hi + W_lo
-//      (W_lo the rounded remainder), written in the A operand's K-major
-//      core-matrix layout;
-//   3. one thread issues tcgen05.mma (kind::f16, FP32 accumulate in TMEM) for
-//      W_hi and W_lo over the three K-steps of 16, then tcgen05.commit to the
-//      batch buffer's mbarrier.
-// Operand buffers are double-buffered: the MMAs of one batch run while the
-// TMA loads and the threads' weights fill the next; a buffer is rewritten only
-// after the mbarrier of the MMAs that read it has completed, and its MMAs are
-// issued only after its load mbarrier has.  At the end of the tile
-// the sixteen warps read the accumulator rows back with tcgen05.ld (warp w
-// sees TMEM lanes 32 (w % 4) ..; warps w, w + 4, w + 8, w + 12 take a quarter
-// of the realizations each) and store d[t][r] = scale * D[t][r].  Every wait on an mbarrier is
-// bounded; on a timeout the kernel records error bit 2, drains what it
-// issued and releases its TMEM.
+// the pair weights of the FP32 kernel.  One CTA (persistent, one per SM) takes
+// tiles of 128 consecutive samples of one detector: the M dimension of the
+// MMA; the realizations are N (up to 256), so the 128 x R FP32 accumulator
+// lives in tensor memory (TMEM) for the whole tile.  The CTA walks the union
+// of the tile's 128 discs ring by ring (the ring-ordered disc query of the
+// FP32 kernel, Sec. 5.2), in batches of 16 union pixels.  Each ring's run of
+// union pixels is cut into blocks of 8 pixels that are consecutive in the
+// RING numbering (a run that wraps past longitude 0 is split there), and a
+// batch is two such blocks.  The contraction index of a batch is map-major,
+// k = 16 m + p (m = I, Q, U; p = pixel of the batch), so that
+//   * the realization rows of one block, [8 pixels][I, Q, U][R] in the stack,
+//     land by one 4-D TMA tile load as the B operand's core matrices
+//     (MN-major, no swizzle: [R/8][3 maps][8 pixels][8 realizations]);
+//   * a thread's four weights of one map are one 8-byte row segment of the A
+//     operand's K-major core matrices.
+//
+// Warp roles (576 threads):
+//   warp 0      one thread issues the MMAs: per batch, for the three maps,
+//               W_hi x S and W_lo x S (kind::f16) into two FP32 accumulators in
+//               TMEM (2 x R columns; the epilogue adds them),
+//               then tcgen05.commit to the stage's "empty" barrier, and at the
+//               tile's end to the accumulator's "full" barrier;
+//   warp 1      the scheduler: per batch, the pixel table (ring, in-ring index,
+//               half-angle of the longitude offset), the two TMA loads of the
+//               realization rows, and the stage's control word;
+//   warps 2-17  the weight producers: thread (sample t, pixel quad q) computes
+//               the FP32 weights of 4 pairs (geometry, 64-byte beam cell, the
+//               Ludwig-3 rotation), splits each into two 16-bit parts
+//               W = W_hi + W_lo (W_lo the rounded remainder) and stores them;
+//               at a tile's end they read the accumulator back (tcgen05.ld)
+//               and write d[t][r] = scale * D[t][r].
+// A ring of NST stages (operand buffers + pixel table + control word) links
+// them through mbarriers: "pixels" (scheduler -> producers), "loads" (TMA
+// bytes + scheduler -> MMA), "full" (16 producer warps -> MMA), "empty" (MMA
+// commit -> scheduler and producers).  The scheduler and the producers meet
+// at a named barrier only where a tile or a chunk of 32 rings begins.
+//
+// Precision of the disc decision.  The FP32 offsets of a pair come from the
+// half-angles of the pixel's and the sample's longitudes relative to the
+// tile's reference; their absolute error grows with those angles.  Per chunk
+// the scheduler bounds the resulting relative error of 1 - k . p0 from the
+// largest half-angles of the chunk's pixels and the tile's samples; where the
+// bound exceeds half of the kernel's FP64 re-decision band (1e-5 relative; tiles
+// whose samples lie far apart, which scans do not produce) the chunk takes the half-angles in FP64
+// (stored as FP32 value + remainder) and forms sin(dphi / 2) as a double-FP32
+// product difference, so every path reaches the FP64 decision of the oracle.
+//
+// Every wait on an mbarrier is bounded (about two seconds of SM clock, or a
+// test-set limit); on a timeout the kernel records error bit 2, every role
+// stops issuing, waits (bounded) for the copies and MMAs it issued, and the
+// block releases its TMEM and returns.
 // Realization stacks are [Npix][3][R] 16-bit (BF16 or FP16), R a multiple of
 // 32 up to 256; the output is FP32 [n][R].
 
@@ -50,59 +71,98 @@ namespace pisco {
 
 namespace {
 
-constexpr int MT = 512;              // threads
-constexpr int MS = 128;              // samples per tile = MMA M
-constexpr int MRC = 32;              // rings per chunk of the union disc
-constexpr int KPIX = 16;             // union pixels per batch
-constexpr int KB = 3 * KPIX;         // contraction length per batch (3 K-steps of 16)
-constexpr int MAXR = 256;            // realizations (MMA N) at most
+constexpr int MS = 128;                   // samples per tile = MMA M
+constexpr int NPW = 16;                   // weight-producer warps
+constexpr int MT = 32 * (2 + NPW);        // threads: MMA warp, scheduler warp, producers
+constexpr int NPT = 32 * NPW;             // producer threads
+constexpr int MRC = 32;                   // rings per chunk of the union
+constexpr int KPIX = 16;                  // union pixels per batch (two blocks of 8)
+constexpr int KB = 3 * KPIX;              // contraction length per batch (3 K-steps of 16)
+constexpr int NST = 4;                    // pipeline stages
+constexpr int MAXR = 256;                 // realizations (MMA N) at most
 // A operand (weights, K-major): core matrix (t / 8, k / 8), 8 rows of 16 bytes
-constexpr int A_LBO = 128;                 // bytes between core matrices adjacent in K
-constexpr int A_SBO = (KB / 8) * 128;      // bytes between core matrices adjacent in M (768)
-constexpr int A_BYTES = MS * KB * 2;       // one 16-bit weight part of a batch (12 KB)
-// B operand (realizations, MN-major): core matrix (k / 8, r / 8), 8 k-rows of 16 bytes
-constexpr int B_SBO = 128;                 // bytes between core matrices adjacent in N
-constexpr int B_BYTES = KB * MAXR * 2;     // a batch's realization rows (24 KB at R = 256)
-// dynamic shared memory: [2 buffers] x (B, A_hi, A_lo)
-constexpr int BUF_BYTES = B_BYTES + 2 * A_BYTES;
-constexpr int MR_DYN_SMEM = 2 * BUF_BYTES + 1024;  // + alignment slack
+constexpr int A_LBO = 128;                // bytes between core matrices adjacent in K
+constexpr int A_SBO = (KB / 8) * 128;     // bytes between core matrices adjacent in M (768)
+constexpr int A_BYTES = MS * KB * 2;      // one 16-bit weight part of a batch (12 KB)
+// B operand (realizations, MN-major): per block [R/8][3 maps][8 pixels][8 realizations]
+constexpr int B_SBO = 3 * 128;            // bytes between core matrices adjacent in N
+__host__ __device__ constexpr int block_bytes(int nreal) { return 48 * nreal; }  // K-adjacent core matrices
+__host__ __device__ constexpr int stage_bytes(int nreal) { return 2 * A_BYTES + 2 * block_bytes(nreal); }
+constexpr int BAR_ID = 1;                 // named barrier of the scheduler and the producers
+constexpr int BAR_N = 32 * (1 + NPW);
+enum { CT_FIRST = 1, CT_LAST = 2, CT_END = 4 };
+constexpr float kEps32 = 5.9604645e-8f;   // FP32 unit roundoff
+constexpr double kBand = 1e-5;            // relative half-width of the FP64 re-decision band
 
-// x split into a rounded 16-bit part and the rounded remainder.
-__device__ __forceinline__ void split16(float x, int f16, unsigned short& hi, unsigned short& lo) {
-    if (f16) {
-        const __half h = __float2half_rn(x);
-        const __half l = __float2half_rn(x - __half2float(h));
-        hi = *reinterpret_cast<const unsigned short*>(&h);
-        lo = *reinterpret_cast<const unsigned short*>(&l);
-    } else {
-        const __nv_bfloat16 h = __float2bfloat16_rn(x);
-        const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
-        hi = *reinterpret_cast<const unsigned short*>(&h);
-        lo = *reinterpret_cast<const unsigned short*>(&l);
-    }
-}
+// Pixel table of one stage (written by the scheduler, read by the producers; 16-byte
+// aligned for the producers' vector reads).
+struct __align__(16) StagePix {
+    float sa[KPIX], ca[KPIX];    // sin, cos of half the pixel's longitude offset from the tile reference
+    float sal[KPIX], cal[KPIX];  // their FP32 remainders (precise chunks)
+    int jw[KPIX];                // in-ring pixel index
+    double theta[2];             // colatitude of block b's ring
+    int ring[2];                 // global ring index of block b
+    int nvalid[2];               // valid pixels of block b (0 .. 8)
+    float sr2[2], inv[2];        // 2 sin(theta_r), 1 / sin^2(theta_r)
+    int ctrl, precise;
+};
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
-__device__ __forceinline__ void mbar_init(unsigned long long* bar) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
 
-// Wait for the mbarrier phase with the given parity; gives up after about two
-// seconds of SM clock and returns false (the caller records the error).
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
-    const unsigned addr = smem_u32(bar);
+__device__ __forceinline__ bool mbar_try(unsigned addr, unsigned parity) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// Wait for the phase of the given parity.  Gives up when the block's failure
+// flag is raised, or after `limit` SM clocks, when it raises the flag and
+// records error bit 2.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, volatile int* failed,
+                                          long long limit, int* err) {
+    const unsigned a = smem_u32(bar);
+    if (mbar_try(a, parity)) return true;
     const long long t0 = clock64();
     while (true) {
-        unsigned done;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-            : "=r"(done)
-            : "r"(addr), "r"(parity)
-            : "memory");
-        if (done) return true;
-        if (clock64() - t0 > 4000000000ll) return false;
+        if (mbar_try(a, parity)) return true;
+        if (*failed) return false;
+        if (clock64() - t0 > limit) {
+            *failed = 1;
+            atomicOr(err, 2);
+            return false;
+        }
     }
+}
+
+// Bounded wait that ignores the failure flag (draining after a failure).
+__device__ __forceinline__ bool mbar_drain(unsigned long long* bar, unsigned parity, long long limit) {
+    const unsigned a = smem_u32(bar);
+    const long long t0 = clock64();
+    while (!mbar_try(a, parity))
+        if (clock64() - t0 > limit) return false;
+    return true;
+}
+
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// The calling thread arrives on the mbarrier and raises its expected transaction count by `bytes`.
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void named_sync() {
+    asm volatile("bar.sync %0, %1;" ::"r"(BAR_ID), "r"(BAR_N) : "memory");
 }
 
 // Shared-memory matrix descriptor of the fifth-generation MMA: start address,
@@ -135,98 +195,24 @@ __device__ __forceinline__ void mma_commit(unsigned long long* bar) {
                  : "memory");
 }
 
-// The calling thread arrives on the mbarrier and raises its expected transaction count by `bytes`.
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
-// TMA tile load of a 3-D tensor's box at coordinates (0, y, 0) into dst, which must
-// be 128-byte aligned; completes `bar`'s transaction count by the box's bytes.
-__device__ __forceinline__ void tma_tile3(void* dst, const CUtensorMap* map, int y, unsigned long long* bar) {
+// TMA tile load of the 4-D realization tensor's box at (0, pix, 0, 0) into dst
+// (128-byte aligned); completes `bar`'s transaction count by the box's bytes.
+__device__ __forceinline__ void tma_tile4(void* dst, const CUtensorMap* map, int pix, unsigned long long* bar) {
     asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
-        "l"((unsigned long long)map), "r"(0), "r"(y), "r"(0), "r"(smem_u32(bar))
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+        "l"((unsigned long long)map), "r"(0), "r"(pix), "r"(0), "r"(0), "r"(smem_u32(bar))
         : "memory");
 }
 
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-
-// Pixel data of union pixel f of the current chunk.
-__device__ __forceinline__ void batch_pixel(int b0, int tid, int nr, int total, const int* sPref, const int* sJlo,
-                                            const int* sRc, const int* sJref, const float* sDph, const float* sAref,
-                                            const int* sFirst, int* bRi, int* bJw, int* bOk, float* bSa, float* bCa,
-                                            long long* bPix, unsigned* bFlag) {
-    const int f = b0 + tid;
-    int ok = f < total;
-    int ri = 0, jw = 0;
-    float sa = 0.f, ca = 1.f;
-    if (ok) {
-        int lo_ = 0, hi_ = nr - 1;
-        while (lo_ < hi_) {
-            const int mid = (lo_ + hi_ + 1) >> 1;
-            if (sPref[mid] <= f) lo_ = mid;
-            else hi_ = mid - 1;
-        }
-        ri = lo_;
-        const int j = sJlo[ri] + (f - sPref[ri]);
-        const int rc = sRc[ri];
-        jw = j % rc;
-        if (jw < 0) jw += rc;
-        const float aa = fmaf((float)(j - sJref[ri]), sDph[ri], sAref[ri]);
-        sincosf(0.5f * aa, &sa, &ca);
-    }
-    const long long pix = ok ? (long long)sFirst[ri] + jw : 0;
-    bRi[tid] = ri;
-    bJw[tid] = jw;
-    bOk[tid] = ok;
-    bSa[tid] = sa;
-    bCa[tid] = ca;
-    bPix[tid] = pix;
-    // core matrix kb holds rows k = 8 kb .. 8 kb + 7 (k = 3 p + m): one TMA tile when its
-    // pixels are valid and consecutive in the stack (rows 3 pix + m then run on)
-    const long long nxt = __shfl_down_sync(0xffffu, pix, 1, KPIX);
-    const unsigned okm = __ballot_sync(0xffffu, ok);
-    const unsigned conm = __ballot_sync(0xffffu, ok && tid < KPIX - 1 && nxt == pix + 1);
-    if (tid == 0) {
-        unsigned fl = 0;
-        for (int kb = 0; kb < KB / 8; ++kb) {
-            const int pa = (8 * kb) / 3, pz = (8 * kb + 7) / 3;
-            const unsigned mo = ((2u << pz) - 1u) & ~((1u << pa) - 1u);  // pixels pa .. pz
-            const unsigned mc = ((1u << pz) - 1u) & ~((1u << pa) - 1u);  // steps pa -> pa + 1 .. pz - 1 -> pz
-            if ((okm & mo) == mo && (conm & mc) == mc) fl |= 1u << kb;
-        }
-        *bFlag = fl;
-    }
-}
-
-// In-frame geometry of one (pixel, sample) pair, as in the FP32 kernel: returns
-// false when the pair is certainly outside the disc (1 - k.p0 above the band).
-struct PairGeom {
-    float w, x, y, fx, fy, flu, flv;
-};
-
-__device__ __forceinline__ bool pair_geometry(const LaunchParams& P, const float4 A4, const float4 B4, const float2 pa,
-                                              float sa, float ca, float sr2, float gmax, PairGeom& g) {
-    const float sh = fmaf(sa, A4.x, -ca * A4.y);
-    const float ch = fmaf(ca, A4.x, sa * A4.y);
-    const float sh2 = sh * sh;
-    g.w = fmaf(B4.y * sr2, sh2, pa.y);
-    if (g.w > P.wr_hi) return false;
-    const float x0 = fmaf(-B4.x * sr2, sh2, pa.x);
-    const float y0 = sr2 * sh * ch;
-    g.x = fmaf(A4.z, x0, A4.w * y0);
-    g.y = fmaf(A4.z, y0, -A4.w * x0);
-    const float fu = fmaf(g.x, P.invh_f, P.cg_f);
-    const float fv = fmaf(g.y, P.invh_f, P.cg_f);
-    g.flu = fminf(fmaxf(floorf(fu), 0.f), gmax);
-    g.flv = fminf(fmaxf(floorf(fv), 0.f), gmax);
-    g.fx = fmaf(g.x, P.invh_f, P.cg_f - g.flu);
-    g.fy = fmaf(g.y, P.invh_f, P.cg_f - g.flv);
-    return true;
+// 64-byte beam cell: one 32-byte and one 16-byte read-only load, not allocated in L1.
+__device__ __forceinline__ void ld_cell(const float* p, float4& a, float4& b, float4& c) {
+    asm("ld.global.nc.L1::no_allocate.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+        : "l"(p));
+    asm("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
+        : "=f"(c.x), "=f"(c.y), "=f"(c.z), "=f"(c.w)
+        : "l"(p + 8));
 }
 
 __device__ __forceinline__ float rcp_approx(float x) {
@@ -235,423 +221,687 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return r;
 }
 
+// Four values as two 16-bit parts each, packed in pairs: hi = rounded value,
+// lo = rounded remainder (element i of a pair in the low half).
+template <int F16>
+__device__ __forceinline__ void split4(const float v[4], uint2& hi, uint2& lo) {
+    unsigned h[2], l[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        if (F16) {
+            const __half2 a = __floats2half2_rn(v[2 * j], v[2 * j + 1]);
+            const float2 af = __half22float2(a);
+            const __half2 b = __floats2half2_rn(v[2 * j] - af.x, v[2 * j + 1] - af.y);
+            h[j] = *reinterpret_cast<const unsigned*>(&a);
+            l[j] = *reinterpret_cast<const unsigned*>(&b);
+        } else {
+            const __nv_bfloat162 a = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+            const float2 af = __bfloat1622float2(a);
+            const __nv_bfloat162 b = __floats2bfloat162_rn(v[2 * j] - af.x, v[2 * j + 1] - af.y);
+            h[j] = *reinterpret_cast<const unsigned*>(&a);
+            l[j] = *reinterpret_cast<const unsigned*>(&b);
+        }
+    }
+    hi = make_uint2(h[0], h[1]);
+    lo = make_uint2(l[0], l[1]);
+}
+
 }  // namespace
 
-// `rows` is the realization stack seen as a 3-D tensor of 16-bit values: element
-// (c, y, q) = realization 8 q + c of row y = 3 p + m (map m of pixel p), with a box of
-// 8 x 8 x R/8 whose shared-memory image [q][8 rows][8] is the B operand's core matrices
-// (k-block, q) at 128-byte strides.
+// `rows` is the realization stack seen as a 4-D tensor of 16-bit values: element
+// (c, p, m, q) = realization 8 q + c of map m of pixel p, with a box of 8 x 8 x 3 x R/8
+// whose shared-memory image [q][m][8 pixels][8] is one block's core matrices.
 template <int F16>
 __global__ void __launch_bounds__(MT, 1) k_mr(const __grid_constant__ LaunchParams P,
                                               const __grid_constant__ CUtensorMap rows) {
+    // per-sample data of the current tile
     __shared__ double sTh[MS], sPh[MS], sPx[MS], sPy[MS], sPz[MS];
-    __shared__ float4 sA[MS], sB[MS];
-    __shared__ float sBf[MS];
+    __shared__ float4 sA[MS];  // cos(b/2), sin(b/2), cos psi0, sin psi0   (b = phi0 - phi_c)
+    __shared__ float4 sB[MS];  // cos theta0, sin theta0, Z_theta, Z_phi
+    __shared__ float2 sBl[MS]; // FP32 remainders of cos(b/2), sin(b/2)
+    __shared__ float sBf[MS];  // b
     __shared__ int sValid[MS];
-    __shared__ int sAny, sRlo, sRhi;
     __shared__ double sPhiC;
-    __shared__ float2 sPA[MRC * MS];
+    __shared__ int sRlo, sRhi, sStop, sNb, sNblocks, sPrecise;
+    __shared__ unsigned sBmax, sS0;  // max |sin(b/2)|, max sin(theta0) (float bits)
+    // chunk of MRC rings: union ranges (producers), tables (scheduler)
     __shared__ float sLo[MRC], sHi[MRC];
-    __shared__ int sFlag[MRC], sJlo[MRC], sJref[MRC], sFirst[MRC], sRc[MRC], sPref[MRC + 1];
-    __shared__ float sAref[MRC], sSr[MRC], sInv[MRC], sDph[MRC];
-    // pixel data of the current and the next batch
-    __shared__ int bRi[2][KPIX], bJw[2][KPIX], bOk[2][KPIX];
-    __shared__ long long bPix[2][KPIX];
-    __shared__ unsigned bFlag[2];  // core matrices of the batch loaded by TMA (bit kb)
-    __shared__ float bSa[2][KPIX], bCa[2][KPIX];
-    __shared__ __align__(8) unsigned long long mbar[2];  // MMAs of buffer b done
-    __shared__ __align__(8) unsigned long long lbar[2];  // TMA loads into buffer b done
+    __shared__ int sFlag[MRC];
+    __shared__ int sJref[MRC], sFirst[MRC];
+    __shared__ float sArefF[MRC], sDphF[MRC], sSr2[MRC], sInv[MRC];
+    __shared__ double sArefD[MRC], sDphD[MRC], sThR[MRC];
+    __shared__ int sEntJw[2 * MRC], sEntJ[2 * MRC], sEntLen[2 * MRC], sEntPref[2 * MRC + 1];
+    // stages
+    __shared__ StagePix sPix[NST];
+    __shared__ __align__(8) unsigned long long bPix[NST], bLoad[NST], bFull[NST], bEmpty[NST];
+    __shared__ __align__(8) unsigned long long bAccFull, bAccEmpty, bFin, bStall;
     __shared__ unsigned tmem_base;
-    __shared__ int failed;
+    __shared__ volatile int failed;
     extern __shared__ unsigned char mr_dyn_raw[];
-    // operand buffers, 1024-byte aligned: buffer b = [B | A_hi | A_lo]
+    // operand stages, 1024-byte aligned: stage s = [A_hi | A_lo | B block 0 | B block 1]
     unsigned char* dyn = mr_dyn_raw + ((1024u - (smem_u32(mr_dyn_raw) & 1023u)) & 1023u);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const unsigned short* __restrict__ sky16 = (const unsigned short*)P.sky;
     const int nreal = P.n_real;
-    const int nc = P.grid_n - 1;
-    const float gmax = (float)(P.grid_n - 2);
-    const int b_lbo = (nreal / 8) * 128;  // B: bytes between core matrices adjacent in K
+    const int sbytes = stage_bytes(nreal);
+    const int bbytes = block_bytes(nreal);
+    // two accumulators of ncols columns: W_hi x S and W_lo x S (the small second one keeps its
+    // rounding errors small; the epilogue adds them)
     const unsigned ncols = nreal <= 32 ? 32u : (nreal <= 64 ? 64u : (nreal <= 128 ? 128u : 256u));
-    const unsigned idesc = instr_desc(F16, nreal, MS);
+    const long long limit = P.wait_limit > 0 ? P.wait_limit : 4000000000ll;
 
-    // zeroed operand buffers, the two mbarriers, the accumulator columns
-    for (int q = tid; q < 2 * BUF_BYTES / 16; q += MT) ((uint4*)dyn)[q] = make_uint4(0u, 0u, 0u, 0u);
+    // zeroed operand stages (a batch whose block has no pixels reads whatever its B buffer
+    // holds, always finite, times zero weights), barriers, accumulator columns
+    for (int q = tid; q < NST * sbytes / 16; q += MT) ((uint4*)dyn)[q] = make_uint4(0u, 0u, 0u, 0u);
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
-                     "r"(ncols)
+                     "r"(2 * ncols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        mbar_init(mbar + 0);
-        mbar_init(mbar + 1);
-        mbar_init(lbar + 0);
-        mbar_init(lbar + 1);
+        for (int s = 0; s < NST; ++s) {
+            mbar_init(bPix + s, 1);
+            mbar_init(bLoad + s, 1);
+            mbar_init(bFull + s, NPW);
+            mbar_init(bEmpty + s, 1);
+        }
+        mbar_init(&bAccFull, 1);
+        mbar_init(&bAccEmpty, NPW);
+        mbar_init(&bFin, 1);
+        mbar_init(&bStall, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         failed = 0;
+        // test hook: wait on a barrier nothing arrives on, before any copy or MMA is issued
+        if (P.stall_cycles > 0) mbar_wait(&bStall, 0, &failed, P.stall_cycles, P.err);
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const unsigned tmem = tmem_base;
-    unsigned phase[2] = {0u, 0u};
-    unsigned lphase[2] = {0u, 0u};  // load mbarrier parities (thread 0 waits on them)
-    bool lfail = false;             // thread 0: a wait for loads timed out (shared flag set before a barrier)
-    bool pend[2] = {false, false};
 
-    // wait for the MMAs that read buffer b (all threads); false after a timeout
-    auto drain = [&](int b) -> bool {
-        if (!pend[b]) return true;
-        pend[b] = false;
-        const bool ok = mbar_wait(mbar + b, phase[b]);
-        phase[b] ^= 1u;
-        return ok;
-    };
-
-    for (long long tile = blockIdx.x; tile < P.total_tiles && !failed; tile += gridDim.x) {
-        int d = 0;
-        while (d + 1 < P.ndet && P.det[d + 1].tile_begin <= tile) ++d;
-        const DetEntry& det = P.det[d];
-        const long long lt = tile - det.tile_begin;
-        const long long t0 = det.begin + lt * MS;
-        const int ns = (int)min((long long)MS, det.count - lt * MS);
-        const float* __restrict__ cells = (const float*)det.beam;
-
-        // 1. per-sample constants (FP64), relative to the first valid sample's longitude
-        if (tid < MS) {
-            const int i = tid;
-            bool ok = i < ns;
-            double th = 0.0, ph = 0.0, ps = 0.0;
-            if (ok) {
-                th = P.theta[t0 + i];
-                ph = P.phi[t0 + i];
-                ps = P.psi[t0 + i];
-                ok = isfinite(th) && isfinite(ph) && isfinite(ps) && th >= 0.0 && th <= kPi;
-            }
-            float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = make_float4(0.f, 0.f, 0.f, 0.f);
-            double px = 0.0, py = 0.0, pz = 0.0, phw = 0.0;
-            if (ok) {
-                phw = ph - kTwoPi * floor(ph / kTwoPi);
-                if (phw >= kTwoPi) phw -= kTwoPi;
-                double st, ct, sp, cp, ss, cs;
-                sincos(th, &st, &ct);
-                sincos(phw, &sp, &cp);
-                sincos(ps, &ss, &cs);
-                px = st * cp;
-                py = st * sp;
-                pz = ct;
-                a.z = (float)cs;
-                a.w = (float)ss;
-                b = make_float4((float)ct, (float)st, (float)(-cs * st), (float)(ss * st));
-            }
-            sTh[i] = th;
-            sPh[i] = phw;
-            sPx[i] = px;
-            sPy[i] = py;
-            sPz[i] = pz;
-            sA[i] = a;
-            sB[i] = b;
-            sValid[i] = ok ? 1 : 0;
-        }
-        __syncthreads();
-        if (tid == 0) {
-            int first = -1;
-            double tmin = 1e9, tmax = -1e9;
-            for (int i = 0; i < MS; ++i)
-                if (sValid[i]) {
-                    if (first < 0) first = i;
-                    tmin = fmin(tmin, sTh[i]);
-                    tmax = fmax(tmax, sTh[i]);
+    if (warp == 0) {
+        // ------------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            const unsigned idesc = instr_desc(F16, nreal, MS);
+            long long it = 0;
+            int tiles = 0;
+            bool pending = false;  // MMAs issued whose completion no one has waited for
+            while (true) {
+                const int s = (int)(it % NST);
+                const unsigned ph = (unsigned)((it / NST) & 1);
+                if (!mbar_wait(bLoad + s, ph, &failed, limit, P.err)) break;
+                const int ctrl = sPix[s].ctrl;
+                if (ctrl & CT_END) break;
+                if (!mbar_wait(bFull + s, ph, &failed, limit, P.err)) break;
+                const bool first = (ctrl & CT_FIRST) != 0;
+                if (first && tiles > 0 && !mbar_wait(&bAccEmpty, (unsigned)((tiles - 1) & 1), &failed, limit, P.err))
+                    break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                unsigned char* st = dyn + s * sbytes;
+                const unsigned ah = smem_u32(st), al = smem_u32(st + A_BYTES), bb = smem_u32(st + 2 * A_BYTES);
+#pragma unroll
+                for (int m = 0; m < 3; ++m) {
+                    const unsigned long long bd = smem_desc(bb + m * 128, (unsigned)bbytes, B_SBO);
+                    const unsigned acc = (first && m == 0) ? 0u : 1u;
+                    mma_f16(tmem, smem_desc(ah + m * 2 * A_LBO, A_LBO, A_SBO), bd, idesc, acc);
+                    mma_f16(tmem + ncols, smem_desc(al + m * 2 * A_LBO, A_LBO, A_SBO), bd, idesc, acc);
                 }
-            sAny = first >= 0;
-            sPhiC = first >= 0 ? sPh[first] : 0.0;
-            int ra = 0, rb = -1;
-            if (first >= 0) ring_range(tmin, tmax, P.radius, P.nside, &ra, &rb);
-            sRlo = ra;
-            sRhi = rb;
+                mma_commit(bEmpty + s);
+                pending = true;
+                if (ctrl & CT_LAST) {
+                    mma_commit(&bAccFull);
+                    ++tiles;
+                    pending = false;  // the producers wait for it before their epilogue
+                }
+                ++it;
+            }
+            if (failed && pending) {
+                // leave no MMA in flight
+                mma_commit(&bFin);
+                mbar_drain(&bFin, 0, limit);
+            }
         }
-        __syncthreads();
-        if (tid < MS && sValid[tid]) {
-            double db = sPh[tid] - sPhiC;
-            db -= kTwoPi * rint(db / kTwoPi);
-            double sb, cb;
-            sincos(0.5 * db, &sb, &cb);
-            sA[tid].x = (float)cb;
-            sA[tid].y = (float)sb;
-            sBf[tid] = (float)db;
-        }
-        __syncthreads();
+        __syncwarp();
+    } else {
+        // ------------------------------------------------------------------ scheduler and producers
+        const bool sched = warp == 1;
+        const int pt = tid - 64;                   // producer thread index (producers only)
+        const int pw = pt >> 5;                    // producer warp 0 .. 15
+        const int my_t = 8 * pw + (lane & 7);      // producer: its sample in the tile
+        const int my_q = lane >> 3;                // producer: its pixel quad (block my_q >> 1)
+        const int nc = P.grid_n - 1;
+        const float gmax = (float)(P.grid_n - 2);
+        const double wr = (double)P.wr_lo / (1.0 - 2e-6);  // 1 - cos R
+        // FP32 membership band of this kernel: pairs with 1 - k . p0 within 1e-5 (relative) of
+        // 1 - cos R take the FP64 decision (about 1e-5 of the pairs)
+        const float wr_lo = (float)(wr * (1.0 - kBand)), wr_hi = (float)(wr * (1.0 + kBand));
+        long long it = 0;                          // stage uses (scheduler and producers count alike)
+        int tile_k = 0;                            // tiles processed (accumulator barrier parity)
+        int sched_issued[NST];                     // scheduler: stage loads issued (drain after a failure)
+#pragma unroll
+        for (int s = 0; s < NST; ++s) sched_issued[s] = 0;
 
-        int batch = 0;  // batches issued in this tile (the first one overwrites the accumulator)
-        const int rlo = sRlo, rhi = sRhi;
-        for (int c0 = rlo; c0 <= rhi && !failed; c0 += MRC) {
-            const int nr = min(MRC, rhi - c0 + 1);
-            // 2. per (ring, sample): sin(dtheta), 1 - cos(dtheta); union of the discs' longitude ranges.
-            //    Thread (ring tid / 16, samples tid % 16 + 16 j).
-            {
-                const int ri = tid >> 4, sub = tid & 15;
-                float lo = __int_as_float(0x7f800000), hi = -__int_as_float(0x7f800000);
-                int full = 0;
-                const bool ring_ok = ri < nr;
-                const RingInfo* R = ring_ok ? &P.rings[c0 + ri] : nullptr;
+        for (long long tile = blockIdx.x; tile < P.total_tiles; tile += gridDim.x) {
+            int d = 0;
+            while (d + 1 < P.ndet && P.det[d + 1].tile_begin <= tile) ++d;
+            const DetEntry& det = P.det[d];
+            const long long lt = tile - det.tile_begin;
+            const long long t0 = det.begin + lt * MS;
+            const int ns = (int)min((long long)MS, det.count - lt * MS);
+            const float* __restrict__ cells = (const float*)det.beam;
+
+            // 1. per-sample constants (FP64 basis, FP32 copies)
+            if (!sched && pt < MS) {
+                const int i = pt;
+                bool ok = i < ns;
+                double th = 0.0, ph = 0.0, ps = 0.0;
+                if (ok) {
+                    th = P.theta[t0 + i];
+                    ph = P.phi[t0 + i];
+                    ps = P.psi[t0 + i];
+                    ok = isfinite(th) && isfinite(ph) && isfinite(ps) && th >= 0.0 && th <= kPi;
+                }
+                float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = make_float4(0.f, 0.f, 0.f, 0.f);
+                double px = 0.0, py = 0.0, pz = 0.0, phw = 0.0;
+                if (ok) {
+                    phw = ph - kTwoPi * floor(ph / kTwoPi);
+                    if (phw >= kTwoPi) phw -= kTwoPi;
+                    double st, ct, sp, cp, ss, cs;
+                    sincos(th, &st, &ct);
+                    sincos(phw, &sp, &cp);
+                    sincos(ps, &ss, &cs);
+                    px = st * cp;
+                    py = st * sp;
+                    pz = ct;
+                    a.z = (float)cs;
+                    a.w = (float)ss;
+                    b = make_float4((float)ct, (float)st, (float)(-cs * st), (float)(ss * st));
+                }
+                sTh[i] = th;
+                sPh[i] = phw;
+                sPx[i] = px;
+                sPy[i] = py;
+                sPz[i] = pz;
+                sA[i] = a;
+                sB[i] = b;
+                sValid[i] = ok ? 1 : 0;
+            }
+            named_sync();
+            if (pt == 0) {
+                int first = -1;
+                double tmin = 1e9, tmax = -1e9, s0 = 0.0;
+                for (int i = 0; i < MS; ++i)
+                    if (sValid[i]) {
+                        if (first < 0) first = i;
+                        tmin = fmin(tmin, sTh[i]);
+                        tmax = fmax(tmax, sTh[i]);
+                        s0 = fmax(s0, (double)sB[i].y);
+                    }
+                sPhiC = first >= 0 ? sPh[first] : 0.0;
+                int ra = 0, rb = -1;
+                if (first >= 0) ring_range(tmin, tmax, P.radius, P.nside, &ra, &rb);
+                sRlo = ra;
+                sRhi = rb;
+                sS0 = __float_as_uint((float)s0);
+                sBmax = 0u;
+                sStop = failed;
+            }
+            named_sync();
+            if (sStop) break;
+            if (!sched && pt < MS && sValid[pt]) {
+                double db = sPh[pt] - sPhiC;
+                db -= kTwoPi * rint(db / kTwoPi);
+                double sb, cb;
+                sincos(0.5 * db, &sb, &cb);
+                const float cbf = (float)cb, sbf = (float)sb;
+                sA[pt].x = cbf;
+                sA[pt].y = sbf;
+                sBl[pt] = make_float2((float)(cb - (double)cbf), (float)(sb - (double)sbf));
+                sBf[pt] = (float)db;
+                atomicMax(&sBmax, __float_as_uint(fabsf(sbf)));
+            }
+            named_sync();
+
+            // producer: its sample's constants for the whole tile
+            float4 A4 = make_float4(0.f, 0.f, 0.f, 0.f), B4 = A4;
+            float2 Bl = make_float2(0.f, 0.f);
+            double th0 = 0.0;
+            bool tvalid = false;
+            if (!sched) {
+                tvalid = sValid[my_t] != 0;
+                A4 = sA[my_t];
+                B4 = sB[my_t];
+                Bl = sBl[my_t];
+                th0 = sTh[my_t];
+            }
+            int pa_ring = -1;
+            float2 pa = make_float2(0.f, 1e30f);
+            bool tile_first = true;
+
+            const int rlo = sRlo, rhi = sRhi;
+            const int nch = rhi >= rlo ? (rhi - rlo) / MRC + 1 : 1;
+            for (int ch = 0; ch < nch; ++ch) {
+                const int c0 = rlo + ch * MRC;
+                const int nr = rhi >= rlo ? min(MRC, rhi - c0 + 1) : 0;
+                const bool last_chunk = ch == nch - 1;
+                // 2. per (ring, sample): union of the discs' longitude ranges (producer (ring pt / 16,
+                //    samples pt % 16 + 16 j))
+                if (!sched) {
+                    const int ri = pt >> 4, sub = pt & 15;
+                    float lo = __int_as_float(0x7f800000), hi = -__int_as_float(0x7f800000);
+                    int full = 0;
+                    const bool ring_ok = ri < nr;
+                    const RingInfo* R = ring_ok ? &P.rings[c0 + ri] : nullptr;
 #pragma unroll 4
-                for (int j = 0; j < MS / 16; ++j) {
-                    const int i = sub + 16 * j;
-                    float2 pa = make_float2(0.f, 1e30f);
-                    if (ring_ok && sValid[i]) {
-                        const float h = (float)(0.5 * (R->theta - sTh[i]));
-                        float sh, ch;
-                        sincosf(h, &sh, &ch);
-                        const float av = 2.f * sh * sh;
-                        pa = make_float2(2.f * sh * ch, av);
-                        if (av <= P.wr_hi) {
-                            const float b2 = 2.f * sB[i].y * R->s_f;
-                            const float tau = (P.wr_hi - av) / b2;
-                            if (!(b2 > 0.f) || !(tau < 0.999f)) {
-                                full = 1;
-                            } else {
-                                const float hw = 2.f * asinf(sqrtf(fmaxf(tau, 0.f)));
-                                lo = fminf(lo, sBf[i] - hw);
-                                hi = fmaxf(hi, sBf[i] + hw);
+                    for (int j = 0; j < MS / 16; ++j) {
+                        const int i = sub + 16 * j;
+                        if (ring_ok && sValid[i]) {
+                            const float h = (float)(0.5 * (R->theta - sTh[i]));
+                            float sh, chh;
+                            sincosf(h, &sh, &chh);
+                            const float av = 2.f * sh * sh;
+                            if (av <= wr_hi) {
+                                const float b2 = 2.f * sB[i].y * R->s_f;
+                                const float tau = (wr_hi - av) / b2;
+                                if (!(b2 > 0.f) || !(tau < 0.999f)) {
+                                    full = 1;
+                                } else {
+                                    const float hw = 2.f * asinf(sqrtf(fmaxf(tau, 0.f)));
+                                    lo = fminf(lo, sBf[i] - hw);
+                                    hi = fmaxf(hi, sBf[i] + hw);
+                                }
                             }
                         }
                     }
-                    sPA[ri * MS + i] = pa;
-                }
 #pragma unroll
-                for (int off = 8; off > 0; off >>= 1) {
-                    lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, off, 16));
-                    hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, off, 16));
-                    full |= __shfl_xor_sync(0xffffffffu, full, off, 16);
+                    for (int off = 8; off > 0; off >>= 1) {
+                        lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, off, 16));
+                        hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, off, 16));
+                        full |= __shfl_xor_sync(0xffffffffu, full, off, 16);
+                    }
+                    if (sub == 0) {
+                        sLo[ri] = lo;
+                        sHi[ri] = hi;
+                        sFlag[ri] = ring_ok ? (full ? 2 : (lo <= hi ? 1 : 0)) : 0;
+                    }
                 }
-                if (sub == 0) {
-                    sLo[ri] = lo;
-                    sHi[ri] = hi;
-                    sFlag[ri] = ring_ok ? (full ? 2 : (lo <= hi ? 1 : 0)) : 0;
-                }
-            }
-            __syncthreads();
-            // 3. per ring: index range of the union, and its prefix over the chunk (one warp)
-            if (warp == 0) {
-                int cnt = 0, jlo = 0, jref = 0, first = 0, rc = 1;
-                float aref = 0.f, sr = 0.f, inv = 0.f, dph = 0.f;
-                if (lane < nr) {
-                    const RingInfo& R = P.rings[c0 + lane];
-                    const int flag = sFlag[lane];
-                    first = (int)R.first;
-                    rc = R.count;
-                    sr = R.s_f;
-                    inv = R.inv_s2_f;
-                    dph = R.dphi_f;
-                    const double phic = sPhiC;
-                    jref = (int)rint((phic - R.phi0) / R.dphi);
-                    aref = (float)(R.phi0 + (double)jref * R.dphi - phic);
-                    if (flag == 2) {
-                        cnt = R.count;
-                        jlo = jref - R.count / 2;
-                    } else if (flag == 1) {
-                        const double ulo = (phic + (double)sLo[lane] - R.phi0) / R.dphi;
-                        const double uhi = (phic + (double)sHi[lane] - R.phi0) / R.dphi;
-                        const long long a = (long long)floor(ulo) - 1, b = (long long)ceil(uhi) + 1;
-                        if (b - a + 1 >= R.count) {
+                named_sync();
+                // 3. scheduler: per ring the index range of the union, split where it wraps past
+                //    longitude 0, in blocks of 8; the precision bound of the chunk
+                if (sched) {
+                    int cnt = 0, jlo = 0, jref = 0, first = 0, rc = 1;
+                    double arefd = 0.0, dphd = 0.0, thr = 0.0;
+                    float sr2 = 0.f, inv = 0.f, amax = 0.f, srmax = 0.f;
+                    if (lane < nr) {
+                        const RingInfo& R = P.rings[c0 + lane];
+                        const int flag = sFlag[lane];
+                        first = (int)R.first;
+                        rc = R.count;
+                        sr2 = 2.f * R.s_f;
+                        inv = R.inv_s2_f;
+                        dphd = R.dphi;
+                        thr = R.theta;
+                        const double phic = sPhiC;
+                        jref = (int)rint((phic - R.phi0) / R.dphi);
+                        arefd = R.phi0 + (double)jref * R.dphi - phic;
+                        if (flag == 2) {
                             cnt = R.count;
                             jlo = jref - R.count / 2;
-                        } else {
-                            cnt = (int)(b - a + 1);
-                            jlo = (int)a;
+                            amax = 1.f;
+                        } else if (flag == 1) {
+                            const double ulo = (phic + (double)sLo[lane] - R.phi0) / R.dphi;
+                            const double uhi = (phic + (double)sHi[lane] - R.phi0) / R.dphi;
+                            const long long a = (long long)floor(ulo) - 1, b = (long long)ceil(uhi) + 1;
+                            if (b - a + 1 >= R.count) {
+                                cnt = R.count;
+                                jlo = jref - R.count / 2;
+                                amax = 1.f;
+                            } else {
+                                cnt = (int)(b - a + 1);
+                                jlo = (int)a;
+                                // largest half-angle of the run's pixels (one pixel of margin each side)
+                                const float ea = fabsf((float)(((double)a - jref) * R.dphi + arefd));
+                                const float eb = fabsf((float)(((double)b - jref) * R.dphi + arefd));
+                                amax = fminf(1.f, fabsf(sinf(0.5f * fminf(fmaxf(ea, eb), 3.1415927f))) + 1e-3f);
+                            }
                         }
+                        if (flag != 0) srmax = R.s_f;
+                    }
+                    int w0 = 0, l1 = 0, l2 = 0;
+                    if (cnt > 0) {
+                        w0 = jlo % rc;
+                        if (w0 < 0) w0 += rc;
+                        l1 = min(cnt, rc - w0);
+                        l2 = cnt - l1;
+                    }
+                    const int b0 = (l1 + 7) >> 3, b1 = (l2 + 7) >> 3;
+                    sJref[lane] = jref;
+                    sFirst[lane] = first;
+                    sArefF[lane] = (float)arefd;
+                    sArefD[lane] = arefd;
+                    sDphF[lane] = (float)dphd;
+                    sDphD[lane] = dphd;
+                    sThR[lane] = thr;
+                    sSr2[lane] = sr2;
+                    sInv[lane] = inv;
+                    sEntJw[2 * lane] = w0;
+                    sEntJ[2 * lane] = jlo;
+                    sEntLen[2 * lane] = l1;
+                    sEntJw[2 * lane + 1] = 0;
+                    sEntJ[2 * lane + 1] = jlo + l1;
+                    sEntLen[2 * lane + 1] = l2;
+                    int v = b0 + b1;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int y = __shfl_up_sync(0xffffffffu, v, o);
+                        if (lane >= o) v += y;
+                    }
+                    const int excl = v - b0 - b1;
+                    sEntPref[2 * lane] = excl;
+                    sEntPref[2 * lane + 1] = excl + b0;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+                        srmax = fmaxf(srmax, __shfl_xor_sync(0xffffffffu, srmax, o));
+                    }
+                    if (lane == 31) {
+                        sEntPref[2 * MRC] = v;
+                        sNblocks = v;
+                        int nb = (v + 1) >> 1;
+                        if (last_chunk && nb == 0) nb = 1;  // every tile ends on a batch flagged last
+                        sNb = nb;
+                        // bound of the relative error of 1 - k . p0 from the FP32 half-angles:
+                        // 16 eps sqrt(k0max / wr) (max |sin a/2| + max |sin b/2|) + 4 eps
+                        const float s0 = __uint_as_float(sS0), bmax = __uint_as_float(sBmax);
+                        const double beta = 16.0 * kEps32 * sqrt(2.0 * s0 * srmax / wr) * (amax + bmax) + 4.0 * kEps32;
+                        sPrecise = beta > 0.5 * kBand ? 1 : 0;
                     }
                 }
-                sJlo[lane] = jlo;
-                sJref[lane] = jref;
-                sFirst[lane] = first;
-                sRc[lane] = rc;
-                sAref[lane] = aref;
-                sSr[lane] = sr;
-                sInv[lane] = inv;
-                sDph[lane] = dph;
-                int v = cnt;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int y = __shfl_up_sync(0xffffffffu, v, o);
-                    if (lane >= o) v += y;
-                }
-                sPref[lane + 1] = v;
-                if (lane == 0) sPref[0] = 0;
-            }
-            __syncthreads();
+                named_sync();
+                const int nb = sNb, nblocks = sNblocks, precise = sPrecise;
 
-            const int total = sPref[nr];
-            // the first batch's pixel data; each batch then prepares the next one's
-            if (tid < KPIX && total > 0)
-                batch_pixel(0, tid, nr, total, sPref, sJlo, sRc, sJref, sDph, sAref, sFirst, bRi[0], bJw[0], bOk[0],
-                            bSa[0], bCa[0], bPix[0], bFlag + 0);
-            __syncthreads();
-            int fb = 0;  // batch within the chunk
-            for (int f0 = 0; f0 < total && !failed; f0 += KPIX, ++batch, ++fb) {
-                const int buf = batch & 1, pb = fb & 1;
-                unsigned char* bB = dyn + buf * BUF_BYTES;
-                unsigned char* bAh = bB + B_BYTES;
-                unsigned char* bAl = bAh + A_BYTES;
-                // the MMAs of two batches ago read this buffer
-                if (!drain(buf) || lfail) atomicOr(&failed, 1);
-                // 4. realization rows into the B operand, core matrix (kb, q) = rows k = 8 kb .. 8 kb + 7
-                //    (k = 3 p + m) x realizations 8 q .. 8 q + 7: by TMA (warp 0) when its rows are
-                //    consecutive in the stack, else as 16-byte chunks (all threads) or zeros
-                {
-                    const int qn = nreal / 8;
-                    const unsigned fl = bFlag[pb];
-                    if (warp == 0) {
-                        if (lane == 0) mbar_expect_tx(lbar + buf, (unsigned)(__popc(fl) * qn * 128));
+                if (sched) {
+                    // 4. scheduler: the stages of this chunk's batches
+                    for (int fb = 0; fb < nb; ++fb, ++it) {
+                        const int s = (int)(it % NST);
+                        const long long u = it / NST;
+                        bool ok = true;
+                        if (lane == 0 && u > 0) ok = mbar_wait(bEmpty + s, (unsigned)((u - 1) & 1), &failed, limit, P.err);
+                        ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0 && !failed;
+                        if (!ok) continue;
+                        StagePix& T = sPix[s];
+                        int nv = 0, pix0 = 0;
+                        if (lane < KPIX) {
+                            const int b = lane >> 3, g = 2 * fb + b;
+                            float sa = 0.f, ca = 1.f, sal = 0.f, cal = 0.f;
+                            int jw = 0;
+                            if (g < nblocks) {
+                                int lo_ = 0, hi_ = 2 * MRC - 1;
+                                while (lo_ < hi_) {
+                                    const int mid = (lo_ + hi_ + 1) >> 1;
+                                    if (sEntPref[mid] <= g) lo_ = mid;
+                                    else hi_ = mid - 1;
+                                }
+                                const int e = lo_, ri = e >> 1;
+                                const int bb = g - sEntPref[e];
+                                const int off = 8 * bb + (lane & 7);
+                                const int len = sEntLen[e];
+                                jw = sEntJw[e] + off;
+                                const int j = sEntJ[e] + off;
+                                if (precise) {
+                                    const double aa = (double)(j - sJref[ri]) * sDphD[ri] + sArefD[ri];
+                                    double sd, cd;
+                                    sincos(0.5 * aa, &sd, &cd);
+                                    sa = (float)sd;
+                                    ca = (float)cd;
+                                    sal = (float)(sd - (double)sa);
+                                    cal = (float)(cd - (double)ca);
+                                } else {
+                                    const float aa = fmaf((float)(j - sJref[ri]), sDphF[ri], sArefF[ri]);
+                                    sincosf(0.5f * aa, &sa, &ca);
+                                }
+                                if ((lane & 7) == 0) {
+                                    nv = min(8, len - 8 * bb);
+                                    pix0 = sFirst[ri] + sEntJw[e] + 8 * bb;
+                                    T.ring[b] = c0 + ri;
+                                    T.theta[b] = sThR[ri];
+                                    T.sr2[b] = sSr2[ri];
+                                    T.inv[b] = sInv[ri];
+                                }
+                            }
+                            T.sa[lane] = sa;
+                            T.ca[lane] = ca;
+                            T.sal[lane] = sal;
+                            T.cal[lane] = cal;
+                            T.jw[lane] = jw;
+                            if ((lane & 7) == 0) T.nvalid[b] = nv;
+                        }
+                        const int nv0 = __shfl_sync(0xffffffffu, nv, 0), nv1 = __shfl_sync(0xffffffffu, nv, 8);
+                        if (lane == 0) {
+                            T.ctrl = (tile_first && fb == 0 ? CT_FIRST : 0) | (last_chunk && fb == nb - 1 ? CT_LAST : 0);
+                            T.precise = precise;
+                        }
                         __syncwarp();
-                        const int kb = lane, k0 = 8 * lane;
-                        if (kb < KB / 8 && ((fl >> kb) & 1u))
-                            tma_tile3(bB + kb * b_lbo, &rows, (int)(bPix[pb][k0 / 3] * 3 + k0 % 3), lbar + buf);
-                    }
-                    if (fl != (1u << (KB / 8)) - 1u) {
-                        for (int c = tid; c < KB * qn; c += MT) {
-                            const int k = c / qn, q = c % qn;
-                            if ((fl >> (k >> 3)) & 1u) continue;
-                            const int p = k / 3, m = k % 3;
-                            unsigned char* dst = bB + (k >> 3) * b_lbo + q * B_SBO + (k & 7) * 16;
-                            if (bOk[pb][p]) cp_async16(dst, sky16 + (bPix[pb][p] * 3 + m) * (long long)nreal + 8 * q);
-                            else *(uint4*)dst = make_uint4(0u, 0u, 0u, 0u);
+                        if (lane == 0) {
+                            mbar_arrive(bPix + s);
+                            mbar_expect_tx(bLoad + s, (unsigned)(((nv0 > 0) + (nv1 > 0)) * bbytes));
                         }
+                        __syncwarp();
+                        if ((lane == 0 || lane == 8) && nv > 0)
+                            tma_tile4(dyn + s * sbytes + 2 * A_BYTES + (lane >> 3) * bbytes, &rows, pix0, bLoad + s);
+                        sched_issued[s] = (int)(u + 1);
                     }
-                    asm volatile("cp.async.commit_group;" ::: "memory");
-                }
-                // 5. pair weights, thread (pixel tid % 16, samples tid / 16 + 32 j), into the A operand
-                {
-                    const int p = tid & (KPIX - 1), tb = tid >> 4;
-                    const bool pok = bOk[pb][p];
-                    const int ri = bRi[pb][p];
-                    const float sr2 = 2.f * sSr[ri], inv = sInv[ri];
-                    const float sa = bSa[pb][p], ca = bCa[pb][p];
+                } else {
+                    // 5. producers: weights of (sample my_t, pixels 4 my_q .. 4 my_q + 3) per batch
+                    const int b = my_q >> 1, half = 4 * (my_q & 1);
+                    for (int fb = 0; fb < nb; ++fb, ++it) {
+                        const int s = (int)(it % NST);
+                        const long long u = it / NST;
+                        bool ok = mbar_wait(bPix + s, (unsigned)(u & 1), &failed, limit, P.err);
+                        if (ok && u > 0) ok = mbar_wait(bEmpty + s, (unsigned)((u - 1) & 1), &failed, limit, P.err);
+                        if (!__all_sync(0xffffffffu, ok)) continue;
+                        const StagePix& T = sPix[s];
+                        const int nv = T.nvalid[b];
+                        float w[3][4];
 #pragma unroll
-                    for (int j = 0; j < MS / 32; ++j) {
-                        const int t = tb + 32 * j;
-                        float wI = 0.f, wQ = 0.f, wU = 0.f;
-                        PairGeom g;
-                        if (pok && sValid[t] &&
-                            pair_geometry(P, sA[t], sB[t], sPA[ri * MS + t], sa, ca, sr2, gmax, g) &&
-                            (g.w <= P.wr_lo ||
-                             exact_in_disc(P.rings, c0 + ri, bJw[pb][p], sPx[t], sPy[t], sPz[t], P.cos_r))) {
-                            const float4 B4 = sB[t];
-                            const float* cp = cells + 16 * ((int)g.flv * nc + (int)g.flu);
-                            const float4 ka = __ldg((const float4*)cp), kb = __ldg((const float4*)(cp + 4));
-                            const float4 kc = __ldg((const float4*)(cp + 8));
-                            const float bA = fmaf(g.fy, fmaf(g.fx, ka.w, ka.z), fmaf(g.fx, ka.y, ka.x));
-                            const float bBq = fmaf(g.fy, fmaf(g.fx, kb.w, kb.z), fmaf(g.fx, kb.y, kb.x));
-                            const float bC = fmaf(g.fy, fmaf(g.fx, kc.w, kc.z), fmaf(g.fx, kc.y, kc.x));
-                            const float qr = rcp_approx(2.f - g.w);
-                            const float mp = fmaf(qr, fmaf(g.x, B4.z, g.y * B4.w), B4.x);
-                            const float e1 = fmaf(-g.x, mp, B4.z);
-                            const float e2 = fmaf(-g.y, mp, B4.w);
-                            const float re = fmaf(e1, e1, -e2 * e2);
-                            const float im2 = e1 * e2;
-                            wI = bA;
-                            wQ = fmaf(bBq, re, 2.f * bC * im2) * inv;
-                            wU = fmaf(bC, re, -2.f * bBq * im2) * inv;
+                        for (int m = 0; m < 3; ++m)
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) w[m][i] = 0.f;
+                        if (tvalid && nv > half) {
+                            const int rg = T.ring[b];
+                            if (rg != pa_ring) {
+                                const float h = (float)(0.5 * (T.theta[b] - th0));
+                                float shh, chh;
+                                sincosf(h, &shh, &chh);
+                                pa = make_float2(2.f * shh * chh, 2.f * shh * shh);
+                                pa_ring = rg;
+                            }
+                            const float sr2 = T.sr2[b], inv = T.inv[b];
+                            const float4 sa4 = *(const float4*)&T.sa[4 * my_q];
+                            const float4 ca4 = *(const float4*)&T.ca[4 * my_q];
+                            const float sav[4] = {sa4.x, sa4.y, sa4.z, sa4.w};
+                            const float cav[4] = {ca4.x, ca4.y, ca4.z, ca4.w};
+                            const bool prec = T.precise != 0;
+                            float4 salv4 = make_float4(0.f, 0.f, 0.f, 0.f), calv4 = salv4;
+                            if (prec) {
+                                salv4 = *(const float4*)&T.sal[4 * my_q];
+                                calv4 = *(const float4*)&T.cal[4 * my_q];
+                            }
+                            const float salv[4] = {salv4.x, salv4.y, salv4.z, salv4.w};
+                            const float calv[4] = {calv4.x, calv4.y, calv4.z, calv4.w};
+                            const float k0 = B4.y * sr2, k1 = -B4.x * sr2;
+                            unsigned band = 0u;  // pairs within the FP32 band of the disc boundary
+                            // two rounds of two pairs: the cell loads of a round are in flight together
+#pragma unroll 1
+                            for (int r2 = 0; r2 < 4; r2 += 2) {
+                                float gx[2], gy[2], gw[2], gfx[2], gfy[2];
+                                bool in[2];
+                                float4 ka[2], kb[2], kc[2];
+#pragma unroll
+                                for (int k = 0; k < 2; ++k) {
+                                    const int i = r2 + k;
+                                    in[k] = false;
+                                    if (half + i >= nv) continue;
+                                    const float sai = r2 == 0 ? (k == 0 ? sav[0] : sav[1]) : (k == 0 ? sav[2] : sav[3]);
+                                    const float cai = r2 == 0 ? (k == 0 ? cav[0] : cav[1]) : (k == 0 ? cav[2] : cav[3]);
+                                    float sh;
+                                    if (prec) {
+                                        // sin((a - b)/2) with the products' rounding errors kept
+                                        const float sli = r2 == 0 ? (k == 0 ? salv[0] : salv[1]) : (k == 0 ? salv[2] : salv[3]);
+                                        const float cli = r2 == 0 ? (k == 0 ? calv[0] : calv[1]) : (k == 0 ? calv[2] : calv[3]);
+                                        const float p1 = sai * A4.x, p2 = cai * A4.y;
+                                        const float e1 = fmaf(sai, A4.x, -p1), e2 = fmaf(cai, A4.y, -p2);
+                                        const float tl = fmaf(sli, A4.x, sai * Bl.x) - fmaf(cli, A4.y, cai * Bl.y);
+                                        sh = (p1 - p2) + (tl + (e1 - e2));
+                                    } else {
+                                        sh = fmaf(sai, A4.x, -cai * A4.y);
+                                    }
+                                    const float chv = fmaf(cai, A4.x, sai * A4.y);
+                                    const float sh2 = sh * sh;
+                                    const float wv = fmaf(k0, sh2, pa.y);  // 1 - k . p0
+                                    if (wv > wr_hi) continue;
+                                    if (wv > wr_lo) band |= 1u << i;  // settled in FP64 below
+                                    const float x0 = fmaf(k1, sh2, pa.x);
+                                    const float y0 = sr2 * sh * chv;
+                                    const float x = fmaf(A4.z, x0, A4.w * y0);   // k . theta'0
+                                    const float y = fmaf(A4.z, y0, -A4.w * x0);  // k . phi'0
+                                    const float flu = fminf(fmaxf(floorf(fmaf(x, P.invh_f, P.cg_f)), 0.f), gmax);
+                                    const float flv = fminf(fmaxf(floorf(fmaf(y, P.invh_f, P.cg_f)), 0.f), gmax);
+                                    gfx[k] = fmaf(x, P.invh_f, P.cg_f - flu);
+                                    gfy[k] = fmaf(y, P.invh_f, P.cg_f - flv);
+                                    gx[k] = x;
+                                    gy[k] = y;
+                                    gw[k] = wv;
+                                    in[k] = true;
+                                    ld_cell(cells + 16 * ((int)flv * nc + (int)flu), ka[k], kb[k], kc[k]);
+                                }
+#pragma unroll
+                                for (int k = 0; k < 2; ++k) {
+                                    if (!in[k]) continue;
+                                    const float fx = gfx[k], fy = gfy[k];
+                                    const float bA = fmaf(fy, fmaf(fx, ka[k].w, ka[k].z), fmaf(fx, ka[k].y, ka[k].x));
+                                    const float bBq = fmaf(fy, fmaf(fx, kb[k].w, kb[k].z), fmaf(fx, kb[k].y, kb[k].x));
+                                    const float bC = fmaf(fy, fmaf(fx, kc[k].w, kc[k].z), fmaf(fx, kc[k].y, kc[k].x));
+                                    const float qr = rcp_approx(2.f - gw[k]);  // 1 / (1 + k . p0)
+                                    const float mp = fmaf(qr, fmaf(gx[k], B4.z, gy[k] * B4.w), B4.x);
+                                    const float e1 = fmaf(-gx[k], mp, B4.z);
+                                    const float e2 = fmaf(-gy[k], mp, B4.w);
+                                    const float re = fmaf(e1, e1, -e2 * e2);
+                                    const float im2 = e1 * e2;
+                                    const float vI = bA;
+                                    const float vQ = fmaf(bBq, re, 2.f * bC * im2) * inv;
+                                    const float vU = fmaf(bC, re, -2.f * bBq * im2) * inv;
+                                    if (r2 == 0) {
+                                        if (k == 0) { w[0][0] = vI; w[1][0] = vQ; w[2][0] = vU; }
+                                        else { w[0][1] = vI; w[1][1] = vQ; w[2][1] = vU; }
+                                    } else {
+                                        if (k == 0) { w[0][2] = vI; w[1][2] = vQ; w[2][2] = vU; }
+                                        else { w[0][3] = vI; w[1][3] = vQ; w[2][3] = vU; }
+                                    }
+                                }
+                            }
+                            // pairs in the band take the FP64 decision shared with the other paths
+                            if (band) {
+#pragma unroll
+                                for (int i = 0; i < 4; ++i)
+                                    if (((band >> i) & 1u) &&
+                                        !exact_in_disc(P.rings, T.ring[b], T.jw[4 * my_q + i], sPx[my_t], sPy[my_t],
+                                                       sPz[my_t], P.cos_r))
+                                        w[0][i] = w[1][i] = w[2][i] = 0.f;
+                            }
                         }
-                        const float wv[3] = {wI, wQ, wU};
+                        // the A operand rows: map m, part hi / lo, 8 bytes at core matrix
+                        // (my_t / 8, 2 m + b), row my_t % 8, bytes 8 (my_q % 2) ..
+                        unsigned char* st = dyn + s * sbytes;
+                        const int off = pw * A_SBO + b * A_LBO + (my_t & 7) * 16 + (my_q & 1) * 8;
 #pragma unroll
                         for (int m = 0; m < 3; ++m) {
-                            const int k = 3 * p + m;
-                            const int off = (t >> 3) * A_SBO + (k >> 3) * A_LBO + (t & 7) * 16 + (k & 7) * 2;
-                            unsigned short h, l;
-                            split16(wv[m], F16, h, l);
-                            *(unsigned short*)(bAh + off) = h;
-                            *(unsigned short*)(bAl + off) = l;
+                            uint2 hi, lo;
+                            split4<F16>(w[m], hi, lo);
+                            *(uint2*)(st + off + m * 2 * A_LBO) = hi;
+                            *(uint2*)(st + A_BYTES + off + m * 2 * A_LBO) = lo;
                         }
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(bFull + s);
                     }
                 }
-                if (tid < KPIX && f0 + KPIX < total)
-                    batch_pixel(f0 + KPIX, tid, nr, total, sPref, sJlo, sRc, sJref, sDph, sAref, sFirst, bRi[pb ^ 1],
-                                bJw[pb ^ 1], bOk[pb ^ 1], bSa[pb ^ 1], bCa[pb ^ 1], bPix[pb ^ 1], bFlag + (pb ^ 1));
-                asm volatile("cp.async.wait_group 0;" ::: "memory");
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                __syncthreads();
-                if (failed) {
-                    // leave no TMA load in flight: thread 0 waits (bounded) for this batch's loads
-                    if (tid == 0) mbar_wait(lbar + buf, lphase[buf]);
-                    break;
-                }
-                // 6. one thread waits for the batch's loads and issues its MMAs:
-                //    D[t][r] += sum_k (W_hi + W_lo)[t][k] S[k][r]; the commit is made even when the
-                //    loads timed out (no MMAs then), so the MMA mbarrier phases stay in step
-                if (tid == 0) {
-                    const bool loaded = mbar_wait(lbar + buf, lphase[buf]);
-                    lphase[buf] ^= 1u;
-                    if (!loaded) {
-                        atomicOr(P.err, 2);
-                        lfail = true;
-                    } else {
-                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll
-                        for (int ks = 0; ks < KB / 16; ++ks) {
-                            const unsigned long long bd = smem_desc(smem_u32(bB + ks * 2 * b_lbo), b_lbo, B_SBO);
-                            const unsigned long long ah = smem_desc(smem_u32(bAh + ks * 2 * A_LBO), A_LBO, A_SBO);
-                            const unsigned long long al = smem_desc(smem_u32(bAl + ks * 2 * A_LBO), A_LBO, A_SBO);
-                            mma_f16(tmem, ah, bd, idesc, (batch > 0 || ks > 0) ? 1u : 0u);
-                            mma_f16(tmem, al, bd, idesc, 1u);
-                        }
-                    }
-                    mma_commit(mbar + buf);
-                }
-                pend[buf] = true;
+                tile_first = tile_first && nb == 0;
+                named_sync();  // the chunk's tables are rewritten next
             }
+
+            // 6. producers: the epilogue, D read back from TMEM (warp w reads lanes 32 (w % 4) ..)
+            if (!sched) {
+                bool ok = true;
+                if (lane == 0) ok = mbar_wait(&bAccFull, (unsigned)(tile_k & 1), &failed, limit, P.err);
+                ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+                if (ok) {
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const int quad = warp & 3, t = 32 * quad + lane;
+                    const int part = nreal / 4;
+                    const int cbeg = ((warp - 2) >> 2) * part;
+                    float* out = (float*)P.out;
+                    const bool row = t < ns;
+                    const bool vrow = row && sValid[t];
+                    for (int c = cbeg; c < cbeg + part; c += 8) {
+                        unsigned r[8], rl[8];
+                        const unsigned addr = tmem + ((unsigned)(32 * quad) << 16) + (unsigned)c;
+                        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                                       "=r"(r[6]), "=r"(r[7])
+                                     : "r"(addr));
+                        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                                     : "=r"(rl[0]), "=r"(rl[1]), "=r"(rl[2]), "=r"(rl[3]), "=r"(rl[4]), "=r"(rl[5]),
+                                       "=r"(rl[6]), "=r"(rl[7])
+                                     : "r"(addr + ncols));
+                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                        if (row) {
+                            float v[8];
+#pragma unroll
+                            for (int j = 0; j < 8; ++j)
+                                v[j] = vrow ? (float)(det.scale * ((double)__uint_as_float(r[j]) + (double)__uint_as_float(rl[j])))
+                                            : __int_as_float(0x7fc00000);
+                            float4* o = (float4*)(out + (t0 + t) * nreal + c);
+                            o[0] = make_float4(v[0], v[1], v[2], v[3]);
+                            o[1] = make_float4(v[4], v[5], v[6], v[7]);
+                        }
+                    }
+                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&bAccEmpty);
+                }
+            }
+            ++tile_k;
         }
 
-        // 7. epilogue: wait for every MMA of the tile, read D back, d = scale * D (NaN for invalid samples)
-        const bool ok0 = drain(0), ok1 = drain(1);
-        if (!ok0 || !ok1 || lfail) {
-            atomicOr(P.err, 2);
-            failed = 1;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        __syncthreads();
-        if (failed) break;
-        {
-            // warp w reads TMEM lanes 32 (w % 4) .. (its samples) and a quarter of the realizations
-            const int t = (warp & 3) * 32 + lane;
-            const int half = nreal / 4;
-            const int cbeg = (warp >> 2) * half;
-            float* out = (float*)P.out;
-            const bool valid_row = t < ns;
-            const bool computed = batch > 0;
-            for (int c = cbeg; c < cbeg + half; c += 8) {
-                unsigned r[8];
-                const unsigned addr = tmem + ((unsigned)((warp & 3) * 32) << 16) + (unsigned)c;
-                asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                             : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-                               "=r"(r[7])
-                             : "r"(addr));
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                if (valid_row) {
-                    float v[8];
-#pragma unroll
-                    for (int j = 0; j < 8; ++j)
-                        v[j] = !sValid[t] ? __int_as_float(0x7fc00000)
-                                          : (computed ? (float)(det.scale * (double)__uint_as_float(r[j])) : 0.f);
-                    float4* o = (float4*)(out + (t0 + t) * nreal + c);
-                    o[0] = make_float4(v[0], v[1], v[2], v[3]);
-                    o[1] = make_float4(v[4], v[5], v[6], v[7]);
+        if (sched) {
+            if (!failed) {
+                // the end marker
+                const int s = (int)(it % NST);
+                const long long u = it / NST;
+                bool ok = true;
+                if (lane == 0 && u > 0) ok = mbar_wait(bEmpty + s, (unsigned)((u - 1) & 1), &failed, limit, P.err);
+                if (lane == 0 && ok) {
+                    sPix[s].ctrl = CT_END;
+                    mbar_expect_tx(bLoad + s, 0u);
                 }
+                __syncwarp();
+            } else if (lane == 0) {
+                // leave no TMA load in flight: wait (bounded) for the last load of every stage
+                for (int s = 0; s < NST; ++s)
+                    if (sched_issued[s] > 0) mbar_drain(bLoad + s, (unsigned)((sched_issued[s] - 1) & 1), limit);
             }
+            __syncwarp();
         }
-        // the next tile's first MMA overwrites the accumulator: all reads done first
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
     }
 
-    // release the accumulator columns (nothing is left in flight: every commit was waited for,
-    // or the wait timed out and the error flag is set)
+    // release the accumulator columns
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * ncols) : "memory");
 }
 
 namespace {
@@ -678,28 +928,38 @@ EncodeTiled encode_tiled() {
 
 cudaError_t launch_mr(const LaunchParams& p, int f16, cudaStream_t s) {
     if (p.total_tiles <= 0) return cudaSuccess;
-    // the stack [3 Npix][R] of 16-bit values as (8 realizations, rows, R / 8 groups): innermost
-    // box extent 16 bytes, every box starts at column 0 of its group (16-byte aligned)
     const EncodeTiled encode = encode_tiled();
-    if (!encode || 3 * p.npix >= INT_MAX || p.n_real % 8 != 0 || p.n_real > 256) return cudaErrorInvalidValue;
+    if (!encode || p.npix >= INT_MAX || p.n_real % 32 != 0 || p.n_real < 32 || p.n_real > MAXR)
+        return cudaErrorInvalidValue;
+    // the stack [Npix][3][R] of 16-bit values as (8 realizations, pixel, map, R / 8 groups): innermost
+    // box extent 16 bytes, every box starts at realization 0 of its pixel (16-byte aligned)
     CUtensorMap rows;
-    const cuuint64_t dims[3] = {8, (cuuint64_t)(3 * p.npix), (cuuint64_t)(p.n_real / 8)};
-    const cuuint64_t strides[2] = {(cuuint64_t)p.n_real * 2, 16};
-    const cuuint32_t box[3] = {8, 8, (cuuint32_t)(p.n_real / 8)}, estr[3] = {1, 1, 1};
-    if (encode(&rows, CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, const_cast<void*>(p.sky), dims, strides, box, estr,
+    const cuuint64_t dims[4] = {8, (cuuint64_t)p.npix, 3, (cuuint64_t)(p.n_real / 8)};
+    const cuuint64_t strides[3] = {(cuuint64_t)p.n_real * 6, (cuuint64_t)p.n_real * 2, 16};
+    const cuuint32_t box[4] = {8, 8, 3, (cuuint32_t)(p.n_real / 8)}, estr[4] = {1, 1, 1, 1};
+    if (encode(&rows, CU_TENSOR_MAP_DATA_TYPE_UINT16, 4, const_cast<void*>(p.sky), dims, strides, box, estr,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
-    const unsigned grid = (unsigned)min(p.total_tiles, (long long)INT_MAX);
+    static int n_sm = 0;
+    if (n_sm == 0) {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess || n_sm <= 0) n_sm = 1;
+    }
+    // persistent: one CTA per SM (the operand stages take most of its shared memory)
+    const unsigned grid = (unsigned)min(p.total_tiles, (long long)n_sm);
+    const int smem = NST * stage_bytes(p.n_real) + 1024;
     cudaError_t e;
     if (f16) {
-        e = cudaFuncSetAttribute(k_mr<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, MR_DYN_SMEM);
+        e = cudaFuncSetAttribute(k_mr<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
-        k_mr<1><<<grid, MT, MR_DYN_SMEM, s>>>(p, rows);
+        k_mr<1><<<grid, MT, smem, s>>>(p, rows);
     } else {
-        e = cudaFuncSetAttribute(k_mr<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, MR_DYN_SMEM);
+        e = cudaFuncSetAttribute(k_mr<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
-        k_mr<0><<<grid, MT, MR_DYN_SMEM, s>>>(p, rows);
+        k_mr<0><<<grid, MT, smem, s>>>(p, rows);
     }
     return cudaGetLastError();
 }

@@ -28,7 +28,7 @@ EXPORTS = ("pisco_plan_create", "pisco_plan_destroy", "pisco_last_error", "pisco
            "pisco_convolve_host", "pisco_sync_status", "pisco_beam_grid_adjoint", "pisco_omega_adjoint",
            "pisco_update_beams", "pisco_beam_grid_adjoint_static", "pisco_convolve_psb",
            "pisco_beam_grids_from_healpix", "pisco_ang2pix", "pisco_map_accumulate", "pisco_map_solve",
-           "pisco_plan_autotune", "pisco_adjoint_sky_beam")
+           "pisco_plan_autotune", "pisco_adjoint_sky_beam", "pisco_inject_mr_stall")
 
 
 class PiscoError(RuntimeError):
@@ -71,6 +71,7 @@ def load_library(path=LIB_PATH):
         "pisco_disc_count": (c_int, [vp, i64, vp, vp, vp, vp]),
         "pisco_convolve_host": (c_int, [vp, c_int, i64, vp, vp, vp, vp]),
         "pisco_sync_status": (c_int, [vp, vp]),
+        "pisco_inject_mr_stall": (c_int, [vp, i64]),
         "pisco_beam_grid_adjoint": (c_int, [vp, c_int, i64, vp, vp, vp, vp, vp, c_int, vp]),
         "pisco_omega_adjoint": (c_int, [vp, c_int, i64, vp, vp, vp, vp]),
         "pisco_update_beams": (c_int, [vp, vp, ctypes.POINTER(dbl), vp]),
@@ -395,6 +396,10 @@ class Plan:
 
     def sync_status(self):
         pisco_sync_status(self.handle)
+
+    def inject_mr_stall(self, cycles):
+        """Test hook: the next multi-realization launch times out on a wait (PISCO_ETIMEOUT)."""
+        _check(load_library().pisco_inject_mr_stall(self.handle, int(cycles)), self.handle)
 
     def close(self):
         if self.handle:

@@ -238,6 +238,38 @@ def healpix_centres(nside):
     return np.concatenate(th), np.concatenate(ph)
 
 
+def pixel_centre_pointings(nside, n, seed):
+    """Pointings exactly on ``n`` seeded RING pixel centres (rho = 0 for that pixel, as in the
+    paper's Table 1 and Sec. 6 runs), with uniform psi; float64 numpy (theta, phi, psi, pix)."""
+    rng = np.random.default_rng(seed)
+    th, ph = healpix_centres(nside)
+    pix = rng.choice(len(th), n, replace=False)
+    return th[pix], ph[pix], rng.uniform(0.0, 2.0 * math.pi, n), pix
+
+
+def disc_edge_pointings(nside, radius, n, seed, delta=1e-12):
+    """Pointings at angular distance radius - delta (even entries) or radius + delta (odd
+    entries) from a seeded RING pixel centre, in a seeded direction: that pixel lies just
+    inside or just outside the pointing's disc.  Pixels are drawn with theta in
+    [radius + 0.05, pi - radius - 0.05] so no pointing reaches a pole.  float64 numpy
+    (theta, phi, psi, pix)."""
+    rng = np.random.default_rng(seed)
+    th, ph = healpix_centres(nside)
+    ok = np.nonzero((th > radius + 0.05) & (th < math.pi - radius - 0.05))[0]
+    pix = rng.choice(ok, n, replace=False)
+    a = rng.uniform(0.0, 2.0 * math.pi, n)
+    dist = radius + np.where(np.arange(n) % 2 == 0, -delta, delta)
+    t, p = th[pix], ph[pix]
+    k = np.stack([np.sin(t) * np.cos(p), np.sin(t) * np.sin(p), np.cos(t)], -1)
+    e_t = np.stack([np.cos(t) * np.cos(p), np.cos(t) * np.sin(p), -np.sin(t)], -1)
+    e_p = np.stack([-np.sin(p), np.cos(p), np.zeros(n)], -1)
+    d = np.cos(a)[:, None] * e_t + np.sin(a)[:, None] * e_p
+    v = np.cos(dist)[:, None] * k + np.sin(dist)[:, None] * d
+    theta0 = np.arctan2(np.hypot(v[:, 0], v[:, 1]), v[:, 2])
+    phi0 = np.mod(np.arctan2(v[:, 1], v[:, 0]), 2.0 * math.pi)
+    return theta0, phi0, rng.uniform(0.0, 2.0 * math.pi, n), pix
+
+
 def focal_plane(n_det, seed, max_offset_deg=10.0):
     """Seeded focal-plane offsets (radians) and beam parameters for ``n_det`` detectors."""
     rng = np.random.default_rng(seed)

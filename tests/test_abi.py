@@ -78,6 +78,7 @@ def test_calls_on_a_null_plan_are_rejected(lib):
     assert lib.pisco_adjoint(None, 0, 0, None, None, None, None, None, 0, None) == pisco.PISCO_EINVAL
     assert lib.pisco_disc_count(None, 0, None, None, None, None) == pisco.PISCO_EINVAL
     assert lib.pisco_sync_status(None, None) == pisco.PISCO_EINVAL
+    assert lib.pisco_inject_mr_stall(None, 1000) == pisco.PISCO_EINVAL
     lib.pisco_plan_destroy(None)
     assert lib.pisco_plan_autotune(None, 0, 10, None, None, None, None, 1, None, None, None, None) == pisco.PISCO_EINVAL
     z = (ctypes.c_double * 2)(0.0, 1.0)

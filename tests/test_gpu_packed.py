@@ -87,7 +87,9 @@ def test_packed_single_detector_workload_sampled():
     th, ph, ps = sy.ces_scan(200000, device=DEV)
     with _plan(nside, r, sky, grids, det) as plan:
         out = plan.convolve(th, ph, ps).double().cpu().numpy()
-        omega = plan.omega(0)[0]
+        plan_omega = plan.omega(0)[0]
+    omega = ob.omega_tilde(grids[0].astype(np.float64), r)
+    assert abs(plan_omega / omega - 1.0) < 1e-12
     idx = np.arange(0, 200000, 1000)
     ref, mag = _oracle(nside, r, sky.cpu().numpy(), grids, det, th.cpu().numpy()[idx], ph.cpu().numpy()[idx],
                        ps.cpu().numpy()[idx], omega)

@@ -59,11 +59,14 @@ def _gpu(nside, radius, sky, grids, dets, theta, phi, psi, precision, tile=0, de
         return out.double().cpu().numpy()
 
 
-def _mixed_pointings(n, seed):
-    """Random pointings, including poles, the longitude wrap and exact pixel centres."""
+def _mixed_pointings(n, seed, nside):
+    """Random pointings, including poles, the longitude wrap and exact pixel centres of the
+    nside sky (rho = 0, as in Table 1 and Sec. 6)."""
     th, ph, ps = sy.random_pointings(n, seed)
     th[:4] = [0.0, math.pi, 1e-7, math.pi - 1e-7]
     ph[4:6] = [-1e-13, 2 * math.pi - 1e-13]
+    tc, pc, _, _ = sy.pixel_centre_pointings(nside, 6, seed)
+    th[6:12], ph[6:12] = tc, pc
     return th, ph, ps
 
 
@@ -74,7 +77,7 @@ def _mixed_pointings(n, seed):
 @pytest.mark.parametrize("nside,radius_deg", [(8, 30.0), (32, 10.0), (64, 5.0)])
 def test_disc_counts_bit_exact(precision, nside, radius_deg):
     r = math.radians(radius_deg)
-    th, ph, ps = _mixed_pointings(150, nside)
+    th, ph, ps = _mixed_pointings(150, nside, nside)
     # add a scan so the FP32 path traverses grouped discs as well
     st, sp, _ = sy.raster_scan(100, center=(1.2, 0.5), half_size=math.radians(2.0), rows=5)
     th, ph = np.concatenate([th, st]), np.concatenate([ph, sp])
@@ -96,7 +99,7 @@ def test_forward_random_beams_random_pointings(precision, rel, nside, radius_deg
     sky = sy.white_sky(nside, 5).numpy()
     grids = sy.random_beam_maps(n_grid, nside + n_grid)
     det = (0.7, 0.08, 1.3)
-    th, ph, ps = _mixed_pointings(70, 3 * nside)
+    th, ph, ps = _mixed_pointings(70, 3 * nside, nside)
     ref, mag = _oracle(nside, r, sky, grids, det, th, ph, ps)
     out = _gpu(nside, r, sky, grids, [det], th, ph, ps, precision)
     np.testing.assert_array_less(np.abs(out - ref), rel * mag + 1e-300)
@@ -185,7 +188,8 @@ def test_batched_focal_plane_equals_single_detector_calls():
                     continue
                 single = plan.convolve(_t(th[a:b]), _t(ph[a:b]), _t(ps[a:b]), det=d).cpu().numpy()
                 np.testing.assert_array_equal(batched[a:b], single)
-                omega = plan.omega(d)[0]
+                omega = ob.omega_tilde(grids[d][0].astype(np.float64), r)
+                assert abs(plan.omega(d)[0] / omega - 1.0) < 1e-12, d
                 ref, mag = _oracle(nside, r, sky, grids[d], dets[d], th[a:b], ph[a:b], ps[a:b], omega)
                 rel = 2e-6 if precision == pisco.PISCO_FP32 else 1e-11
                 np.testing.assert_array_less(np.abs(single - ref), rel * mag)
@@ -267,12 +271,13 @@ def test_fp32_single_detector_workload_sampled():
     th, ph, ps = sy.ces_scan(200000, device=DEV)
     with pisco.Plan(nside, r, sky, [det], torch.as_tensor(grids, device=DEV)[None]) as plan:
         out = plan.convolve(th, ph, ps).double().cpu().numpy()
-        omega = plan.omega(0)[0]
+        plan_omega = plan.omega(0)[0]
     idx = np.arange(0, 200000, 1000)
     skyn = sky.cpu().numpy()
+    omega = ob.omega_tilde(grids[0].astype(np.float64), r)
+    assert abs(plan_omega / omega - 1) < 1e-12
     ref, mag = _oracle(nside, r, skyn, grids, det, th.cpu().numpy()[idx], ph.cpu().numpy()[idx],
                        ps.cpu().numpy()[idx], omega)
-    assert abs(omega / ob.omega_tilde(grids[0].astype(np.float64), r) - 1) < 1e-12
     np.testing.assert_array_less(np.abs(out[idx] - ref), 2e-6 * mag)
     assert np.max(np.abs(out[idx] - ref)) <= 1e-6 * np.max(np.abs(ref))
 
@@ -293,8 +298,11 @@ def test_focal_plane_configuration_batched_sampled():
     offsets = [0] + list(np.cumsum(lengths))
     with pisco.Plan(nside, r, sky, dets, torch.as_tensor(grids, device=DEV).contiguous()) as plan:
         out = plan.convolve_batched(offsets, th, ph, ps).double().cpu().numpy()
-        omegas = [plan.omega(d)[0] for d in range(n_det)]
+        plan_omegas = [plan.omega(d)[0] for d in range(n_det)]
         plan.sync_status()
+    omegas = [ob.omega_tilde(grids[d][0].astype(np.float64), r) for d in range(n_det)]
+    for d in range(n_det):
+        assert abs(plan_omegas[d] / omegas[d] - 1.0) < 1e-12, d
     skyn, thn, phn, psn = sky.cpu().numpy(), th.cpu().numpy(), ph.cpu().numpy(), ps.cpu().numpy()
     for d in range(n_det):
         idx = offsets[d] + np.array([0, lengths[d] // 2, lengths[d] - 1])
