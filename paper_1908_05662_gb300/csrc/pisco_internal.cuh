@@ -70,6 +70,8 @@ struct LaunchParams {
     int n_zeta;            // shared-geometry pass: number of polarisation angles
     long long out_stride;  // shared-geometry pass: elements between the TODs of two angles
     float psb_c2z[kMaxPsb], psb_s2z[kMaxPsb];  // cos, sin of 2 (zeta_k - zeta of the plan's detector)
+    double mr_wr;            // multi-realization kernel: 1 - cos R, and its FP32 re-decision band edges
+    float mr_wr_lo, mr_wr_hi;
     long long wait_limit;    // multi-realization kernel: SM clocks a wait on an mbarrier may take (0: ~2 s)
     long long stall_cycles;  // multi-realization kernel, test hook: > 0 makes it wait this long, before it
                              // issues any copy or MMA, on an mbarrier nothing arrives on (a timeout)

@@ -47,8 +47,8 @@
 // tile's reference; their absolute error grows with those angles.  Per chunk
 // the scheduler bounds the resulting relative error of 1 - k . p0 from the
 // largest half-angles of the chunk's pixels and the tile's samples; where the
-// bound exceeds half of the kernel's FP64 re-decision band (1e-5 relative; tiles
-// whose samples lie far apart, which scans do not produce) the chunk takes the half-angles in FP64
+// bound exceeds the kernel's FP64 re-decision band (2e-5 relative; tiles whose
+// samples lie far apart, which scans do not produce) the chunk takes the half-angles in FP64
 // (stored as FP32 value + remainder) and forms sin(dphi / 2) as a double-FP32
 // product difference, so every path reaches the FP64 decision of the oracle.
 //
@@ -79,6 +79,8 @@ constexpr int MRC = 32;                   // rings per chunk of the union
 constexpr int KPIX = 16;                  // union pixels per batch (two blocks of 8)
 constexpr int KB = 3 * KPIX;              // contraction length per batch (3 K-steps of 16)
 constexpr int NST = 4;                    // pipeline stages
+static_assert((NST & (NST - 1)) == 0, "NST is a power of two");
+constexpr int WINB = NPT / 16;            // batches per pixel-table window (one pixel per producer thread)
 constexpr int MAXR = 256;                 // realizations (MMA N) at most
 // A operand (weights, K-major): core matrix (t / 8, k / 8), 8 rows of 16 bytes
 constexpr int A_LBO = 128;                // bytes between core matrices adjacent in K
@@ -92,20 +94,8 @@ constexpr int BAR_ID = 1;                 // named barrier of the scheduler and 
 constexpr int BAR_N = 32 * (1 + NPW);
 enum { CT_FIRST = 1, CT_LAST = 2, CT_END = 4 };
 constexpr float kEps32 = 5.9604645e-8f;   // FP32 unit roundoff
-constexpr double kBand = 1e-5;            // relative half-width of the FP64 re-decision band
-
-// Pixel table of one stage (written by the scheduler, read by the producers; 16-byte
-// aligned for the producers' vector reads).
-struct __align__(16) StagePix {
-    float sa[KPIX], ca[KPIX];    // sin, cos of half the pixel's longitude offset from the tile reference
-    float sal[KPIX], cal[KPIX];  // their FP32 remainders (precise chunks)
-    int jw[KPIX];                // in-ring pixel index
-    double theta[2];             // colatitude of block b's ring
-    int ring[2];                 // global ring index of block b
-    int nvalid[2];               // valid pixels of block b (0 .. 8)
-    float sr2[2], inv[2];        // 2 sin(theta_r), 1 / sin^2(theta_r)
-    int ctrl, precise;
-};
+constexpr double kBand = 2e-5;            // relative half-width of the FP64 re-decision band (the
+                                          // launcher sets the band edges from it)
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -271,9 +261,17 @@ __global__ void __launch_bounds__(MT, 1) k_mr(const __grid_constant__ LaunchPara
     __shared__ float sArefF[MRC], sDphF[MRC], sSr2[MRC], sInv[MRC];
     __shared__ double sArefD[MRC], sDphD[MRC], sThR[MRC];
     __shared__ int sEntJw[2 * MRC], sEntJ[2 * MRC], sEntLen[2 * MRC], sEntPref[2 * MRC + 1];
+    // pixel table of a window of WINB batches (filled by the producers, one pixel per thread)
+    __shared__ __align__(16) float wSa[NPT];
+    __shared__ __align__(16) float wCa[NPT];
+    __shared__ __align__(16) float wSal[NPT];
+    __shared__ __align__(16) float wCal[NPT];
+    __shared__ int wJw[NPT];
+    __shared__ int wNv[NPT / 8], wPix0[NPT / 8], wRing[NPT / 8];
+    __shared__ float wThh[NPT / 8], wThl[NPT / 8], wSr2[NPT / 8], wInv[NPT / 8];
     // stages
-    __shared__ StagePix sPix[NST];
-    __shared__ __align__(8) unsigned long long bPix[NST], bLoad[NST], bFull[NST], bEmpty[NST];
+    __shared__ int sCtrl[NST];
+    __shared__ __align__(8) unsigned long long bLoad[NST], bFull[NST], bEmpty[NST];
     __shared__ __align__(8) unsigned long long bAccFull, bAccEmpty, bFin, bStall;
     __shared__ unsigned tmem_base;
     __shared__ volatile int failed;
@@ -301,7 +299,6 @@ __global__ void __launch_bounds__(MT, 1) k_mr(const __grid_constant__ LaunchPara
     }
     if (tid == 0) {
         for (int s = 0; s < NST; ++s) {
-            mbar_init(bPix + s, 1);
             mbar_init(bLoad + s, 1);
             mbar_init(bFull + s, NPW);
             mbar_init(bEmpty + s, 1);
@@ -325,14 +322,14 @@ __global__ void __launch_bounds__(MT, 1) k_mr(const __grid_constant__ LaunchPara
         // ------------------------------------------------------------------ MMA issuer
         if (lane == 0) {
             const unsigned idesc = instr_desc(F16, nreal, MS);
-            long long it = 0;
+            unsigned it = 0;
             int tiles = 0;
             bool pending = false;  // MMAs issued whose completion no one has waited for
             while (true) {
                 const int s = (int)(it % NST);
-                const unsigned ph = (unsigned)((it / NST) & 1);
+                const unsigned ph = (it / NST) & 1u;
                 if (!mbar_wait(bLoad + s, ph, &failed, limit, P.err)) break;
-                const int ctrl = sPix[s].ctrl;
+                const int ctrl = sCtrl[s];
                 if (ctrl & CT_END) break;
                 if (!mbar_wait(bFull + s, ph, &failed, limit, P.err)) break;
                 const bool first = (ctrl & CT_FIRST) != 0;
@@ -373,15 +370,12 @@ __global__ void __launch_bounds__(MT, 1) k_mr(const __grid_constant__ LaunchPara
         const int my_q = lane >> 3;                // producer: its pixel quad (block my_q >> 1)
         const int nc = P.grid_n - 1;
         const float gmax = (float)(P.grid_n - 2);
-        const double wr = (double)P.wr_lo / (1.0 - 2e-6);  // 1 - cos R
-        // FP32 membership band of this kernel: pairs with 1 - k . p0 within 1e-5 (relative) of
-        // 1 - cos R take the FP64 decision (about 1e-5 of the pairs)
-        const float wr_lo = (float)(wr * (1.0 - kBand)), wr_hi = (float)(wr * (1.0 + kBand));
-        long long it = 0;                          // stage uses (scheduler and producers count alike)
+        const double wr = P.mr_wr;  // 1 - cos R
+        // FP32 membership band of this kernel: pairs with 1 - k . p0 within 2e-5 (relative) of
+        // 1 - cos R take the FP64 decision (a few 1e-5 of the pairs)
+        const float wr_hi = P.mr_wr_hi;
+        unsigned it = 0;                           // stage uses (scheduler and producers count alike)
         int tile_k = 0;                            // tiles processed (accumulator barrier parity)
-        int sched_issued[NST];                     // scheduler: stage loads issued (drain after a failure)
-#pragma unroll
-        for (int s = 0; s < NST; ++s) sched_issued[s] = 0;
 
         for (long long tile = blockIdx.x; tile < P.total_tiles; tile += gridDim.x) {
             int d = 0;
@@ -467,14 +461,15 @@ __global__ void __launch_bounds__(MT, 1) k_mr(const __grid_constant__ LaunchPara
             // producer: its sample's constants for the whole tile
             float4 A4 = make_float4(0.f, 0.f, 0.f, 0.f), B4 = A4;
             float2 Bl = make_float2(0.f, 0.f);
-            double th0 = 0.0;
+            float th0h = 0.f, th0l = 0.f;  // the sample's colatitude as FP32 value + remainder
             bool tvalid = false;
             if (!sched) {
                 tvalid = sValid[my_t] != 0;
                 A4 = sA[my_t];
                 B4 = sB[my_t];
                 Bl = sBl[my_t];
-                th0 = sTh[my_t];
+                th0h = (float)sTh[my_t];
+                th0l = (float)(sTh[my_t] - (double)th0h);
             }
             int pa_ring = -1;
             float2 pa = make_float2(0.f, 1e30f);
@@ -612,203 +607,186 @@ __global__ void __launch_bounds__(MT, 1) k_mr(const __grid_constant__ LaunchPara
                         int nb = (v + 1) >> 1;
                         if (last_chunk && nb == 0) nb = 1;  // every tile ends on a batch flagged last
                         sNb = nb;
-                        // bound of the relative error of 1 - k . p0 from the FP32 half-angles:
-                        // 16 eps sqrt(k0max / wr) (max |sin a/2| + max |sin b/2|) + 4 eps
-                        const float s0 = __uint_as_float(sS0), bmax = __uint_as_float(sBmax);
-                        const double beta = 16.0 * kEps32 * sqrt(2.0 * s0 * srmax / wr) * (amax + bmax) + 4.0 * kEps32;
-                        sPrecise = beta > 0.5 * kBand ? 1 : 0;
+                        // bound of the relative error of 1 - k . p0 from the FP32 half-angles
+                        // (A = max |sin a/2| of the chunk's pixels, B = max |sin b/2| of the tile's
+                        // samples, k0 = 2 sin theta0 sin theta_r):
+                        //   beta <= 14 u + 2 u sqrt(k0 / wr) (6.2 A + 4 B + 3.2 A B)
+                        // with u the FP32 unit roundoff; the fast path needs beta <= the band
+                        const double s0 = __uint_as_float(sS0), bmax = __uint_as_float(sBmax), am = amax;
+                        const double beta = 14.0 * kEps32 + 2.0 * kEps32 * sqrt(2.0 * s0 * srmax / wr) *
+                                                                (6.2 * am + 4.0 * bmax + 3.2 * am * bmax);
+                        sPrecise = beta > kBand ? 1 : 0;
                     }
                 }
                 named_sync();
                 const int nb = sNb, nblocks = sNblocks, precise = sPrecise;
 
+                // the chunk's batches, in windows of WINB batches (2 WINB blocks, one pixel per
+                // producer thread): the producers first fill the window's pixel table together
+                for (int wb0 = 0; wb0 < nb; wb0 += WINB) {
+                    const int wnb = min(WINB, nb - wb0);
+                    if (!sched) {
+                        // 4. pixel pt of the window: block g = 2 wb0 + pt / 8, pixel pt % 8 of the block
+                        const int g = 2 * wb0 + (pt >> 3), pp = pt & 7;
+                        float sa = 0.f, ca = 1.f, sal = 0.f, cal = 0.f;
+                        int jw = 0;
+                        if (g < nblocks) {
+                            int lo_ = 0, hi_ = 2 * MRC - 1;
+                            while (lo_ < hi_) {
+                                const int mid = (lo_ + hi_ + 1) >> 1;
+                                if (sEntPref[mid] <= g) lo_ = mid;
+                                else hi_ = mid - 1;
+                            }
+                            const int e = lo_, ri = e >> 1;
+                            const int bb = g - sEntPref[e];
+                            const int off = 8 * bb + pp;
+                            jw = sEntJw[e] + off;
+                            const int j = sEntJ[e] + off;
+                            if (precise) {
+                                const double aa = (double)(j - sJref[ri]) * sDphD[ri] + sArefD[ri];
+                                double sd, cd;
+                                sincos(0.5 * aa, &sd, &cd);
+                                sa = (float)sd;
+                                ca = (float)cd;
+                                sal = (float)(sd - (double)sa);
+                                cal = (float)(cd - (double)ca);
+                            } else {
+                                const float aa = fmaf((float)(j - sJref[ri]), sDphF[ri], sArefF[ri]);
+                                sincosf(0.5f * aa, &sa, &ca);
+                            }
+                            if (pp == 0) {
+                                const int wbk = pt >> 3;
+                                wNv[wbk] = min(8, sEntLen[e] - 8 * bb);
+                                wPix0[wbk] = sFirst[ri] + sEntJw[e] + 8 * bb;
+                                wRing[wbk] = c0 + ri;
+                                const float th_h = (float)sThR[ri];
+                                wThh[wbk] = th_h;
+                                wThl[wbk] = (float)(sThR[ri] - (double)th_h);
+                                wSr2[wbk] = sSr2[ri];
+                                wInv[wbk] = sInv[ri];
+                            }
+                        } else if (pp == 0) {
+                            wNv[pt >> 3] = 0;
+                        }
+                        wSa[pt] = sa;
+                        wCa[pt] = ca;
+                        wSal[pt] = sal;
+                        wCal[pt] = cal;
+                        wJw[pt] = jw;
+                    }
+                    named_sync();
+
                 if (sched) {
-                    // 4. scheduler: the stages of this chunk's batches
-                    for (int fb = 0; fb < nb; ++fb, ++it) {
+                    // 5. scheduler: the stages of the window's batches (control word, TMA loads)
+                    for (int fb = wb0; fb < wb0 + wnb; ++fb, ++it) {
                         const int s = (int)(it % NST);
-                        const long long u = it / NST;
+                        const unsigned u = it / NST;
                         bool ok = true;
                         if (lane == 0 && u > 0) ok = mbar_wait(bEmpty + s, (unsigned)((u - 1) & 1), &failed, limit, P.err);
                         ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0 && !failed;
                         if (!ok) continue;
-                        StagePix& T = sPix[s];
-                        int nv = 0, pix0 = 0;
-                        if (lane < KPIX) {
-                            const int b = lane >> 3, g = 2 * fb + b;
-                            float sa = 0.f, ca = 1.f, sal = 0.f, cal = 0.f;
-                            int jw = 0;
-                            if (g < nblocks) {
-                                int lo_ = 0, hi_ = 2 * MRC - 1;
-                                while (lo_ < hi_) {
-                                    const int mid = (lo_ + hi_ + 1) >> 1;
-                                    if (sEntPref[mid] <= g) lo_ = mid;
-                                    else hi_ = mid - 1;
-                                }
-                                const int e = lo_, ri = e >> 1;
-                                const int bb = g - sEntPref[e];
-                                const int off = 8 * bb + (lane & 7);
-                                const int len = sEntLen[e];
-                                jw = sEntJw[e] + off;
-                                const int j = sEntJ[e] + off;
-                                if (precise) {
-                                    const double aa = (double)(j - sJref[ri]) * sDphD[ri] + sArefD[ri];
-                                    double sd, cd;
-                                    sincos(0.5 * aa, &sd, &cd);
-                                    sa = (float)sd;
-                                    ca = (float)cd;
-                                    sal = (float)(sd - (double)sa);
-                                    cal = (float)(cd - (double)ca);
-                                } else {
-                                    const float aa = fmaf((float)(j - sJref[ri]), sDphF[ri], sArefF[ri]);
-                                    sincosf(0.5f * aa, &sa, &ca);
-                                }
-                                if ((lane & 7) == 0) {
-                                    nv = min(8, len - 8 * bb);
-                                    pix0 = sFirst[ri] + sEntJw[e] + 8 * bb;
-                                    T.ring[b] = c0 + ri;
-                                    T.theta[b] = sThR[ri];
-                                    T.sr2[b] = sSr2[ri];
-                                    T.inv[b] = sInv[ri];
-                                }
-                            }
-                            T.sa[lane] = sa;
-                            T.ca[lane] = ca;
-                            T.sal[lane] = sal;
-                            T.cal[lane] = cal;
-                            T.jw[lane] = jw;
-                            if ((lane & 7) == 0) T.nvalid[b] = nv;
-                        }
-                        const int nv0 = __shfl_sync(0xffffffffu, nv, 0), nv1 = __shfl_sync(0xffffffffu, nv, 8);
+                        const int wbk0 = 2 * (fb - wb0);
+                        const int nv0 = wNv[wbk0], nv1 = wNv[wbk0 + 1];
                         if (lane == 0) {
-                            T.ctrl = (tile_first && fb == 0 ? CT_FIRST : 0) | (last_chunk && fb == nb - 1 ? CT_LAST : 0);
-                            T.precise = precise;
-                        }
-                        __syncwarp();
-                        if (lane == 0) {
-                            mbar_arrive(bPix + s);
+                            sCtrl[s] = (tile_first && fb == 0 ? CT_FIRST : 0) | (last_chunk && fb == nb - 1 ? CT_LAST : 0);
                             mbar_expect_tx(bLoad + s, (unsigned)(((nv0 > 0) + (nv1 > 0)) * bbytes));
                         }
                         __syncwarp();
-                        if ((lane == 0 || lane == 8) && nv > 0)
-                            tma_tile4(dyn + s * sbytes + 2 * A_BYTES + (lane >> 3) * bbytes, &rows, pix0, bLoad + s);
-                        sched_issued[s] = (int)(u + 1);
+                        if (lane < 2 && (lane == 0 ? nv0 : nv1) > 0)
+                            tma_tile4(dyn + s * sbytes + 2 * A_BYTES + lane * bbytes, &rows, wPix0[wbk0 + lane], bLoad + s);
                     }
                 } else {
-                    // 5. producers: weights of (sample my_t, pixels 4 my_q .. 4 my_q + 3) per batch
+                    // 6. producers: weights of (sample my_t, pixels 4 my_q .. 4 my_q + 3) per batch
                     const int b = my_q >> 1, half = 4 * (my_q & 1);
-                    for (int fb = 0; fb < nb; ++fb, ++it) {
+                    for (int fb = wb0; fb < wb0 + wnb; ++fb, ++it) {
                         const int s = (int)(it % NST);
-                        const long long u = it / NST;
-                        bool ok = mbar_wait(bPix + s, (unsigned)(u & 1), &failed, limit, P.err);
-                        if (ok && u > 0) ok = mbar_wait(bEmpty + s, (unsigned)((u - 1) & 1), &failed, limit, P.err);
+                        const unsigned u = it / NST;
+                        bool ok = true;
+                        if (u > 0) ok = mbar_wait(bEmpty + s, (unsigned)((u - 1) & 1), &failed, limit, P.err);
                         if (!__all_sync(0xffffffffu, ok)) continue;
-                        const StagePix& T = sPix[s];
-                        const int nv = T.nvalid[b];
+                        const int wbk = 2 * (fb - wb0) + b;  // the thread's block in the window
+                        const int px0 = 8 * wbk + half;       // its first pixel in the window
+                        const int nv = wNv[wbk];
                         float w[3][4];
 #pragma unroll
                         for (int m = 0; m < 3; ++m)
 #pragma unroll
                             for (int i = 0; i < 4; ++i) w[m][i] = 0.f;
                         if (tvalid && nv > half) {
-                            const int rg = T.ring[b];
+                            const int rg = wRing[wbk];
                             if (rg != pa_ring) {
-                                const float h = (float)(0.5 * (T.theta[b] - th0));
+                                // half the colatitude difference: the FP32 values of nearby rings
+                                // subtract exactly, the remainders restore the rest
+                                const float h = 0.5f * ((wThh[wbk] - th0h) + (wThl[wbk] - th0l));
                                 float shh, chh;
                                 sincosf(h, &shh, &chh);
                                 pa = make_float2(2.f * shh * chh, 2.f * shh * shh);
                                 pa_ring = rg;
                             }
-                            const float sr2 = T.sr2[b], inv = T.inv[b];
-                            const float4 sa4 = *(const float4*)&T.sa[4 * my_q];
-                            const float4 ca4 = *(const float4*)&T.ca[4 * my_q];
+                            const float sr2 = wSr2[wbk], inv = wInv[wbk];
+                            const float4 sa4 = *(const float4*)&wSa[px0];
+                            const float4 ca4 = *(const float4*)&wCa[px0];
                             const float sav[4] = {sa4.x, sa4.y, sa4.z, sa4.w};
                             const float cav[4] = {ca4.x, ca4.y, ca4.z, ca4.w};
-                            const bool prec = T.precise != 0;
+                            const bool prec = precise != 0;
                             float4 salv4 = make_float4(0.f, 0.f, 0.f, 0.f), calv4 = salv4;
                             if (prec) {
-                                salv4 = *(const float4*)&T.sal[4 * my_q];
-                                calv4 = *(const float4*)&T.cal[4 * my_q];
+                                salv4 = *(const float4*)&wSal[px0];
+                                calv4 = *(const float4*)&wCal[px0];
                             }
                             const float salv[4] = {salv4.x, salv4.y, salv4.z, salv4.w};
                             const float calv[4] = {calv4.x, calv4.y, calv4.z, calv4.w};
                             const float k0 = B4.y * sr2, k1 = -B4.x * sr2;
+                            const float wlo = P.mr_wr_lo, whi = P.mr_wr_hi;
                             unsigned band = 0u;  // pairs within the FP32 band of the disc boundary
-                            // two rounds of two pairs: the cell loads of a round are in flight together
-#pragma unroll 1
-                            for (int r2 = 0; r2 < 4; r2 += 2) {
-                                float gx[2], gy[2], gw[2], gfx[2], gfy[2];
-                                bool in[2];
-                                float4 ka[2], kb[2], kc[2];
 #pragma unroll
-                                for (int k = 0; k < 2; ++k) {
-                                    const int i = r2 + k;
-                                    in[k] = false;
-                                    if (half + i >= nv) continue;
-                                    const float sai = r2 == 0 ? (k == 0 ? sav[0] : sav[1]) : (k == 0 ? sav[2] : sav[3]);
-                                    const float cai = r2 == 0 ? (k == 0 ? cav[0] : cav[1]) : (k == 0 ? cav[2] : cav[3]);
-                                    float sh;
-                                    if (prec) {
-                                        // sin((a - b)/2) with the products' rounding errors kept
-                                        const float sli = r2 == 0 ? (k == 0 ? salv[0] : salv[1]) : (k == 0 ? salv[2] : salv[3]);
-                                        const float cli = r2 == 0 ? (k == 0 ? calv[0] : calv[1]) : (k == 0 ? calv[2] : calv[3]);
-                                        const float p1 = sai * A4.x, p2 = cai * A4.y;
-                                        const float e1 = fmaf(sai, A4.x, -p1), e2 = fmaf(cai, A4.y, -p2);
-                                        const float tl = fmaf(sli, A4.x, sai * Bl.x) - fmaf(cli, A4.y, cai * Bl.y);
-                                        sh = (p1 - p2) + (tl + (e1 - e2));
-                                    } else {
-                                        sh = fmaf(sai, A4.x, -cai * A4.y);
-                                    }
-                                    const float chv = fmaf(cai, A4.x, sai * A4.y);
-                                    const float sh2 = sh * sh;
-                                    const float wv = fmaf(k0, sh2, pa.y);  // 1 - k . p0
-                                    if (wv > wr_hi) continue;
-                                    if (wv > wr_lo) band |= 1u << i;  // settled in FP64 below
-                                    const float x0 = fmaf(k1, sh2, pa.x);
-                                    const float y0 = sr2 * sh * chv;
-                                    const float x = fmaf(A4.z, x0, A4.w * y0);   // k . theta'0
-                                    const float y = fmaf(A4.z, y0, -A4.w * x0);  // k . phi'0
-                                    const float flu = fminf(fmaxf(floorf(fmaf(x, P.invh_f, P.cg_f)), 0.f), gmax);
-                                    const float flv = fminf(fmaxf(floorf(fmaf(y, P.invh_f, P.cg_f)), 0.f), gmax);
-                                    gfx[k] = fmaf(x, P.invh_f, P.cg_f - flu);
-                                    gfy[k] = fmaf(y, P.invh_f, P.cg_f - flv);
-                                    gx[k] = x;
-                                    gy[k] = y;
-                                    gw[k] = wv;
-                                    in[k] = true;
-                                    ld_cell(cells + 16 * ((int)flv * nc + (int)flu), ka[k], kb[k], kc[k]);
+                            for (int i = 0; i < 4; ++i) {
+                                if (half + i >= nv) continue;
+                                float sh;
+                                if (prec) {
+                                    // sin((a - b)/2) with the products' rounding errors kept
+                                    const float p1 = sav[i] * A4.x, p2 = cav[i] * A4.y;
+                                    const float e1 = fmaf(sav[i], A4.x, -p1), e2 = fmaf(cav[i], A4.y, -p2);
+                                    const float tl = fmaf(salv[i], A4.x, sav[i] * Bl.x) - fmaf(calv[i], A4.y, cav[i] * Bl.y);
+                                    sh = (p1 - p2) + (tl + (e1 - e2));
+                                } else {
+                                    sh = fmaf(sav[i], A4.x, -cav[i] * A4.y);
                                 }
-#pragma unroll
-                                for (int k = 0; k < 2; ++k) {
-                                    if (!in[k]) continue;
-                                    const float fx = gfx[k], fy = gfy[k];
-                                    const float bA = fmaf(fy, fmaf(fx, ka[k].w, ka[k].z), fmaf(fx, ka[k].y, ka[k].x));
-                                    const float bBq = fmaf(fy, fmaf(fx, kb[k].w, kb[k].z), fmaf(fx, kb[k].y, kb[k].x));
-                                    const float bC = fmaf(fy, fmaf(fx, kc[k].w, kc[k].z), fmaf(fx, kc[k].y, kc[k].x));
-                                    const float qr = rcp_approx(2.f - gw[k]);  // 1 / (1 + k . p0)
-                                    const float mp = fmaf(qr, fmaf(gx[k], B4.z, gy[k] * B4.w), B4.x);
-                                    const float e1 = fmaf(-gx[k], mp, B4.z);
-                                    const float e2 = fmaf(-gy[k], mp, B4.w);
-                                    const float re = fmaf(e1, e1, -e2 * e2);
-                                    const float im2 = e1 * e2;
-                                    const float vI = bA;
-                                    const float vQ = fmaf(bBq, re, 2.f * bC * im2) * inv;
-                                    const float vU = fmaf(bC, re, -2.f * bBq * im2) * inv;
-                                    if (r2 == 0) {
-                                        if (k == 0) { w[0][0] = vI; w[1][0] = vQ; w[2][0] = vU; }
-                                        else { w[0][1] = vI; w[1][1] = vQ; w[2][1] = vU; }
-                                    } else {
-                                        if (k == 0) { w[0][2] = vI; w[1][2] = vQ; w[2][2] = vU; }
-                                        else { w[0][3] = vI; w[1][3] = vQ; w[2][3] = vU; }
-                                    }
-                                }
+                                const float chv = fmaf(cav[i], A4.x, sav[i] * A4.y);
+                                const float sh2 = sh * sh;
+                                const float wv = fmaf(k0, sh2, pa.y);  // 1 - k . p0
+                                if (wv > whi) continue;
+                                if (wv > wlo) band |= 1u << i;  // settled in FP64 below
+                                const float x0 = fmaf(k1, sh2, pa.x);
+                                const float y0 = sr2 * sh * chv;
+                                const float x = fmaf(A4.z, x0, A4.w * y0);   // k . theta'0
+                                const float y = fmaf(A4.z, y0, -A4.w * x0);  // k . phi'0
+                                const float flu = fminf(fmaxf(floorf(fmaf(x, P.invh_f, P.cg_f)), 0.f), gmax);
+                                const float flv = fminf(fmaxf(floorf(fmaf(y, P.invh_f, P.cg_f)), 0.f), gmax);
+                                const float fx = fmaf(x, P.invh_f, P.cg_f - flu);
+                                const float fy = fmaf(y, P.invh_f, P.cg_f - flv);
+                                float4 ka, kb, kc;
+                                ld_cell(cells + 16 * ((int)flv * nc + (int)flu), ka, kb, kc);
+                                const float bA = fmaf(fy, fmaf(fx, ka.w, ka.z), fmaf(fx, ka.y, ka.x));
+                                const float bBq = fmaf(fy, fmaf(fx, kb.w, kb.z), fmaf(fx, kb.y, kb.x));
+                                const float bC = fmaf(fy, fmaf(fx, kc.w, kc.z), fmaf(fx, kc.y, kc.x));
+                                const float qr = rcp_approx(2.f - wv);  // 1 / (1 + k . p0)
+                                const float mp = fmaf(qr, fmaf(x, B4.z, y * B4.w), B4.x);
+                                const float e1 = fmaf(-x, mp, B4.z);
+                                const float e2 = fmaf(-y, mp, B4.w);
+                                const float re = fmaf(e1, e1, -e2 * e2);
+                                const float im2 = e1 * e2;
+                                w[0][i] = bA;
+                                w[1][i] = fmaf(bBq, re, 2.f * bC * im2) * inv;
+                                w[2][i] = fmaf(bC, re, -2.f * bBq * im2) * inv;
                             }
                             // pairs in the band take the FP64 decision shared with the other paths
                             if (band) {
 #pragma unroll
                                 for (int i = 0; i < 4; ++i)
                                     if (((band >> i) & 1u) &&
-                                        !exact_in_disc(P.rings, T.ring[b], T.jw[4 * my_q + i], sPx[my_t], sPy[my_t],
-                                                       sPz[my_t], P.cos_r))
+                                        !exact_in_disc(P.rings, rg, wJw[px0 + i], sPx[my_t], sPy[my_t], sPz[my_t],
+                                                       P.cos_r))
                                         w[0][i] = w[1][i] = w[2][i] = 0.f;
                             }
                         }
@@ -828,6 +806,8 @@ __global__ void __launch_bounds__(MT, 1) k_mr(const __grid_constant__ LaunchPara
                         if (lane == 0) mbar_arrive(bFull + s);
                     }
                 }
+                named_sync();  // the window's table is rewritten next
+                }
                 tile_first = tile_first && nb == 0;
                 named_sync();  // the chunk's tables are rewritten next
             }
@@ -843,6 +823,7 @@ __global__ void __launch_bounds__(MT, 1) k_mr(const __grid_constant__ LaunchPara
                     const int part = nreal / 4;
                     const int cbeg = ((warp - 2) >> 2) * part;
                     float* out = (float*)P.out;
+                    const float scale_f = (float)det.scale;
                     const bool row = t < ns;
                     const bool vrow = row && sValid[t];
                     for (int c = cbeg; c < cbeg + part; c += 8) {
@@ -861,7 +842,7 @@ __global__ void __launch_bounds__(MT, 1) k_mr(const __grid_constant__ LaunchPara
                             float v[8];
 #pragma unroll
                             for (int j = 0; j < 8; ++j)
-                                v[j] = vrow ? (float)(det.scale * ((double)__uint_as_float(r[j]) + (double)__uint_as_float(rl[j])))
+                                v[j] = vrow ? scale_f * (__uint_as_float(r[j]) + __uint_as_float(rl[j]))
                                             : __int_as_float(0x7fc00000);
                             float4* o = (float4*)(out + (t0 + t) * nreal + c);
                             o[0] = make_float4(v[0], v[1], v[2], v[3]);
@@ -880,18 +861,18 @@ __global__ void __launch_bounds__(MT, 1) k_mr(const __grid_constant__ LaunchPara
             if (!failed) {
                 // the end marker
                 const int s = (int)(it % NST);
-                const long long u = it / NST;
+                const unsigned u = it / NST;
                 bool ok = true;
                 if (lane == 0 && u > 0) ok = mbar_wait(bEmpty + s, (unsigned)((u - 1) & 1), &failed, limit, P.err);
                 if (lane == 0 && ok) {
-                    sPix[s].ctrl = CT_END;
+                    sCtrl[s] = CT_END;
                     mbar_expect_tx(bLoad + s, 0u);
                 }
                 __syncwarp();
             } else if (lane == 0) {
                 // leave no TMA load in flight: wait (bounded) for the last load of every stage
                 for (int s = 0; s < NST; ++s)
-                    if (sched_issued[s] > 0) mbar_drain(bLoad + s, (unsigned)((sched_issued[s] - 1) & 1), limit);
+                    if (it > (unsigned)s) mbar_drain(bLoad + s, ((it - 1 - s) / NST) & 1u, limit);
             }
             __syncwarp();
         }
@@ -926,8 +907,13 @@ EncodeTiled encode_tiled() {
 
 }  // namespace
 
-cudaError_t launch_mr(const LaunchParams& p, int f16, cudaStream_t s) {
-    if (p.total_tiles <= 0) return cudaSuccess;
+cudaError_t launch_mr(const LaunchParams& p0, int f16, cudaStream_t s) {
+    if (p0.total_tiles <= 0) return cudaSuccess;
+    LaunchParams p = p0;
+    const double wr = 2.0 * sin(0.5 * p.radius) * sin(0.5 * p.radius);  // 1 - cos R
+    p.mr_wr = wr;
+    p.mr_wr_lo = (float)(wr * (1.0 - kBand));
+    p.mr_wr_hi = (float)(wr * (1.0 + kBand));
     const EncodeTiled encode = encode_tiled();
     if (!encode || p.npix >= INT_MAX || p.n_real % 32 != 0 || p.n_real < 32 || p.n_real > MAXR)
         return cudaErrorInvalidValue;
