@@ -66,12 +66,16 @@ def measured_peaks(path=os.path.join(ROOT, "MEASURED_PEAKS.json")):
 
 HBM_GBS, BF16_TFLOPS, PEAK_SOURCE = measured_peaks()
 
-# DRAM bytes (read + write) of one forward launch on the default single-detector workload
-# (1e7 samples, 16-sample tiles, 1 pixel per thread, 64-byte cells) from one ncu capture of
-# dram__bytes_read.sum + dram__bytes_write.sum (1 pass, full-size launch): 486.63 MB read,
-# 47.03 MB written.  Pointing (240 MB) and TOD (40 MB) stream through once; the rest is the
-# L2-resident sky and beam cells, some re-read after the pointing stream evicts them.
-FORWARD_TRAFFIC_BYTES = {(10_000_000, 16, 1): 486.63e6 + 47.03e6}
+# Recorded ncu figures of the forward launch on the default single-detector workload, keyed by
+# (samples, tile_samples, pixels_per_thread) with 64-byte cells; they are not measured by this run:
+# * traffic: dram__bytes_read.sum + dram__bytes_write.sum of one full-size launch (1 pass):
+#   486.63 MB read, 47.03 MB written.  Pointing (240 MB) and TOD (40 MB) stream through once; the
+#   rest is the L2-resident sky and beam cells, some re-read after the pointing stream evicts them;
+# * l1tex / lts: l1tex__throughput.avg.pct_of_peak_sustained_active and
+#   lts__throughput.avg.pct_of_peak_sustained_elapsed of the same kernel shape on a 5e5-sample
+#   slice (profiles/k_fast_forward_single_detector.md): the unit that binds is the L1/TEX path
+#   serving scattered 32-byte sectors of beam cells.
+FORWARD_PROFILE = {(10_000_000, 16, 1): {"traffic": 486.63e6 + 47.03e6, "l1tex_pct": 93.1, "lts_pct": 78.1}}
 
 
 def parse():
@@ -351,6 +355,13 @@ def run_focalplane(args, dev):
     offsets = [0] + list(np.cumsum(lengths))
     n = int(offsets[-1])
     plan = pisco.Plan(nside, r, sky, dets, torch.as_tensor(grids, device=dev).contiguous())
+    # tile shape from the batched autotuner on the first 2e4 samples of every detector (untimed)
+    m_tune = 20_000
+    tune_idx = torch.cat([torch.arange(offsets[d], offsets[d] + min(m_tune, int(lengths[d])), device=dev)
+                          for d in range(n_det)])
+    tune_off = [0] + list(np.cumsum([min(m_tune, int(x)) for x in lengths]))
+    tuned = plan.autotune_batched(tune_off, th[tune_idx].contiguous(), ph[tune_idx].contiguous(),
+                                  ps[tune_idx].contiguous(), reps=2)
     pairs = int(plan.disc_count(th, ph).to(torch.int64).sum().item())
     tod = torch.empty(n, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
@@ -406,6 +417,9 @@ def run_focalplane(args, dev):
            "config": {"workload": "focal plane: 64 detectors, offsets +-10 deg, FWHM 1.2-1.8 deg, e 0-0.1, "
                                   "201^2 grids of radius 6 deg, scan lengths U[1e5, 5e6], nside 256",
                       "samples": n, "pairs_per_step": pairs, "launch": "cuda graph" if graph else "eager",
+                      "tile_samples": tuned[0], "pixels_per_thread": tuned[1],
+                      "tile_shape": "autotuned (pisco_plan_autotune_batched on the first 2e4 samples of every "
+                                    "detector)",
                       "l2": "inputs larger than L2"},
            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                         "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None},
@@ -616,10 +630,14 @@ def run_grad(args, dev):
     from oracle import beam as ob
     from oracle import convolve as oc
     from paper_1908_05662_gb300 import autograd as pag
+    import torch.distributed as tdist
+    distributed = tdist.is_available() and tdist.is_initialized()
+    world = tdist.get_world_size() if distributed else 1
+    rank = tdist.get_rank() if distributed else 0
     nside, r, n_grid = 512, math.radians(5.0), 201
-    n = args.samples
+    n = args.samples  # per rank: weak scaling, rank k takes samples k n .. (k + 1) n - 1 of the scan
     sky = cached_sky(nside, 1, dev)
-    th, ph, ps = (a.contiguous() for a in sy.ces_scan(n, device=dev))
+    th, ph, ps = (a.contiguous() for a in sy.ces_scan(n, device=dev, start=rank * n))
     det = (0.0, 0.0, 1.0)
     p0, pt = (1.5, 0.05, 0.005), (1.52, 0.06, 0.004)
 
@@ -635,11 +653,27 @@ def run_grad(args, dev):
         sky_t = sky.clone().requires_grad_(True)
         loss = ((tod_of(params, sky_t, th, ph, ps).double() - target) ** 2).sum()
         loss.backward()
+        if world > 1:
+            # the transposes are sums over all samples: one all-reduce of each gradient
+            tdist.all_reduce(sky_t.grad)
+            tdist.all_reduce(params.grad)
         return params.grad, sky_t.grad
 
     stream = torch.cuda.current_stream()
+    if world > 1:
+        tdist.barrier()
     with ClockSampler(torch.cuda.current_device()) as clocks:
         ms = _event_time(step, args.steps, args.warmup, stream)
+    ms = max_over_ranks(ms, dev)
+    # the collective alone: the sky-map gradient (3 x Npix FP32) and the beam-grid gradient
+    grad_maps = torch.zeros(3, 12 * nside * nside, device=dev)
+    grad_grid = torch.zeros(6, n_grid, n_grid, device=dev)
+    allreduce_ms = 0.0
+    if world > 1:
+        allreduce_ms = max_over_ranks(_event_time(lambda: (tdist.all_reduce(grad_maps), tdist.all_reduce(grad_grid)),
+                                                  args.steps, 1, stream), dev)
+        if rank != 0:
+            return
     # the passes one by one on the same inputs
     g = beams.gaussian_beam_grids(n_grid, r, *p0, device=dev).float()[None].contiguous()
     y = torch.randn(n, device=dev)
@@ -690,9 +724,13 @@ def run_grad(args, dev):
         fd.append((chi2(np.array(p0) + e) - chi2(np.array(p0) - e)) / (2 * h))
     rel = [abs(grad[i] - fd[i]) / abs(fd[i]) for i in range(3)]
     bg = parts["sky_and_beam_adjoint_ms"]
-    out = {"metric": "gradient steps/s (TOD, chi^2, backward to sky maps and beam parameters; 1e7 samples)",
-           "value": 1e3 / ms, "unit": "steps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-           "ms_per_step": ms, "samples_per_s": n / (ms / 1e3), "higher_is_better": True, "scaling": "weak",
+    out = {"metric": "gradient steps/s (TOD, chi^2, backward to sky maps and beam parameters; 1e7 samples per GPU)",
+           "value": 1e3 / ms, "unit": "steps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": ms, "samples_per_s": world * n / (ms / 1e3), "higher_is_better": True, "scaling": "weak",
+           "allreduce": {"ms": allreduce_ms, "share_of_step": allreduce_ms / ms,
+                         "bytes": 4 * (3 * 12 * nside * nside + 6 * n_grid * n_grid),
+                         "note": "one all-reduce of the sky-map gradient and one of the beam-grid gradient "
+                                 "(NCCL; zero on one GPU)"},
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": "differentiation: nside 512, parametric beam (FWHM 1.5 deg, e 0.05, l 0.005), "
                                   "R 5 deg, 201^2 grid, 1e7 scan samples", "samples": n, "pairs_per_pass": pairs},
@@ -787,6 +825,8 @@ def main():
         {"c1": run_c1, "focalplane": run_focalplane, "multireal": run_multireal, "table1": run_table1, "psb": run_psb,
          "sec61": run_sec61, "grad": run_grad}[args.workload](
             args, torch.device("cuda", local))
+        if world > 1:
+            torch.distributed.destroy_process_group()
         return
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -873,6 +913,7 @@ def main():
     out = None
     if rank == 0:
         achieved_tflops = FLOPS_PER_PAIR * pairs / (ms / 1e3) / 1e12
+        recorded = FORWARD_PROFILE.get((n, tuned[0], tuned[1]), {})
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -885,8 +926,14 @@ def main():
                        "l2": "inputs larger than L2 (pointing 24 B/sample = 240 MB)"},
             "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": FP32_PEAK_TFLOPS,
                          "unit": "TFLOP/s", "frac": achieved_tflops / FP32_PEAK_TFLOPS,
-                         "traffic": FORWARD_TRAFFIC_BYTES.get((n, tuned[0], tuned[1])),
-                         "traffic_note": "ncu DRAM bytes read + written per forward launch",
+                         "traffic": recorded.get("traffic"),
+                         "traffic_note": "recorded ncu capture of DRAM bytes read + written per forward launch "
+                                         "of this shape (null for another shape); not measured by this run",
+                         "binding_unit": "L1/TEX (scattered 32-byte sectors of beam cells, all L2 hits)",
+                         "l1tex_throughput_pct": recorded.get("l1tex_pct"),
+                         "lts_throughput_pct": recorded.get("lts_pct"),
+                         "unit_pct_note": "recorded ncu percentages of peak for this kernel shape "
+                                          "(profiles/k_fast_forward_single_detector.md)",
                          "kernel": f"pisco::k_fast<{tuned[0]}, {tuned[1]}, cells, forward>",
                          "peak_note": "FP32 from unit counts: 152 SM x 128 lanes x 2 x 2070 MHz",
                          "hbm_frac": (28 * n / (ms / 1e3)) / (HBM_GBS * 1e9), "hbm_peak_source": PEAK_SOURCE},

@@ -399,6 +399,20 @@ pisco_status pisco_plan_autotune(pisco_plan* plan, int det, int64_t n,
  */
 pisco_status pisco_inject_mr_stall(pisco_plan* plan, int64_t cycles);
 
+/*
+ * pisco_plan_autotune_batched -- pisco_plan_autotune for a focal plane (Sec.
+ * 5.1): every shape runs pisco_convolve_batched on the given slices of the
+ * detectors' scans (offsets: host [n_det + 1], as in pisco_convolve_batched;
+ * e.g. the first 1e4 - 1e5 samples of every detector), and the plan keeps the
+ * fastest shape for all its detectors.  tod_scratch: device float32
+ * [offsets[n_det]], overwritten.  Other arguments, outputs and errors as for
+ * pisco_plan_autotune.
+ */
+pisco_status pisco_plan_autotune_batched(pisco_plan* plan, int n_det, const int64_t* offsets,
+                                         const double* theta, const double* phi, const double* psi,
+                                         void* tod_scratch, int reps, int* tile_samples,
+                                         int* pixels_per_thread, float* best_ms, void* stream);
+
 /* Synchronise the plan's work on `stream` and report any error a kernel
  * recorded since the last call, clearing it: PISCO_ETIMEOUT when a bounded
  * device wait gave up (flag 2: the multi-realization kernel waits about two

@@ -28,7 +28,8 @@ EXPORTS = ("pisco_plan_create", "pisco_plan_destroy", "pisco_last_error", "pisco
            "pisco_convolve_host", "pisco_sync_status", "pisco_beam_grid_adjoint", "pisco_omega_adjoint",
            "pisco_update_beams", "pisco_beam_grid_adjoint_static", "pisco_convolve_psb",
            "pisco_beam_grids_from_healpix", "pisco_ang2pix", "pisco_map_accumulate", "pisco_map_solve",
-           "pisco_plan_autotune", "pisco_adjoint_sky_beam", "pisco_inject_mr_stall")
+           "pisco_plan_autotune", "pisco_adjoint_sky_beam", "pisco_inject_mr_stall",
+           "pisco_plan_autotune_batched")
 
 
 class PiscoError(RuntimeError):
@@ -85,6 +86,9 @@ def load_library(path=LIB_PATH):
         "pisco_adjoint_sky_beam": (c_int, [vp, c_int, i64, vp, vp, vp, vp, vp, vp, c_int, vp]),
         "pisco_plan_autotune": (c_int, [vp, c_int, i64, vp, vp, vp, vp, c_int, ctypes.POINTER(c_int),
                                         ctypes.POINTER(c_int), ctypes.POINTER(ctypes.c_float), vp]),
+        "pisco_plan_autotune_batched": (c_int, [vp, c_int, ctypes.POINTER(i64), vp, vp, vp, vp, c_int,
+                                                ctypes.POINTER(c_int), ctypes.POINTER(c_int),
+                                                ctypes.POINTER(ctypes.c_float), vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -202,6 +206,19 @@ def pisco_plan_autotune(plan, det, theta, phi, psi, reps=2):
     _check(load_library().pisco_plan_autotune(plan, det, theta.numel(), _ptr(_f64(theta)), _ptr(_f64(phi)),
                                               _ptr(_f64(psi)), _ptr(scratch), int(reps), ctypes.byref(t),
                                               ctypes.byref(p), ctypes.byref(ms), _stream()), plan)
+    return t.value, p.value, ms.value
+
+
+def pisco_plan_autotune_batched(plan, offsets, theta, phi, psi, reps=2):
+    """Time the FP32 tile shapes on a focal plane's slices (offsets as for convolve_batched); the
+    plan keeps the fastest.  Returns (tile_samples, pixels_per_thread, ms per launch)."""
+    n_det = len(offsets) - 1
+    off = (ctypes.c_int64 * (n_det + 1))(*[int(x) for x in offsets])
+    scratch = torch.empty(theta.numel(), dtype=torch.float32, device=theta.device)
+    t, p, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
+    _check(load_library().pisco_plan_autotune_batched(plan, n_det, off, _ptr(_f64(theta)), _ptr(_f64(phi)),
+                                                      _ptr(_f64(psi)), _ptr(scratch), int(reps), ctypes.byref(t),
+                                                      ctypes.byref(p), ctypes.byref(ms), _stream()), plan)
     return t.value, p.value, ms.value
 
 
@@ -350,6 +367,10 @@ class Plan:
     def autotune(self, theta, phi, psi, det=0, reps=2):
         """Pick the FP32 tile shape by timing it on these pointings: (tile_samples, pixels_per_thread, ms)."""
         return pisco_plan_autotune(self.handle, det, theta, phi, psi, reps)
+
+    def autotune_batched(self, offsets, theta, phi, psi, reps=2):
+        """Pick the FP32 tile shape by timing a focal-plane slice: (tile_samples, pixels_per_thread, ms)."""
+        return pisco_plan_autotune_batched(self.handle, offsets, theta, phi, psi, reps)
 
     def convolve_batched(self, offsets, theta, phi, psi, out=None):
         if out is None:

@@ -190,8 +190,9 @@ def raster_scan(n, center=(math.radians(60.0), math.radians(45.0)), half_size=ma
 
 def ces_scan(n, rate_hz=20.0, latitude_deg=-23.0, elevation_deg=45.0, az_speed_deg=1.0,
              az_span_deg=720.0, boresight_deg=(-45.0, -30.0, -15.0, 0.0, 15.0, 30.0, 45.0),
-             lst0=0.0, offset=None, device="cpu"):
-    """Constant-elevation azimuth scan, float64 (theta, phi, psi) torch tensors.
+             lst0=0.0, offset=None, device="cpu", start=0):
+    """Constant-elevation azimuth scan, float64 (theta, phi, psi) torch tensors: samples
+    start .. start + n - 1 of the scan.
 
     The azimuth sweeps a triangle wave over ``az_span_deg`` at ``az_speed_deg``
     per second; the sky turns at the sidereal rate; the boresight angle
@@ -200,7 +201,7 @@ def ces_scan(n, rate_hz=20.0, latitude_deg=-23.0, elevation_deg=45.0, az_speed_d
     the boresight in the focal plane (dx along the elevation axis).
     """
     f64 = torch.float64
-    t = torch.arange(n, dtype=f64, device=device) / rate_hz
+    t = torch.arange(start, start + n, dtype=f64, device=device) / rate_hz
     period = 2.0 * az_span_deg / az_speed_deg
     ph = torch.remainder(t, period) / period
     az = torch.deg2rad(az_span_deg * torch.where(ph < 0.5, 2.0 * ph, 2.0 - 2.0 * ph))

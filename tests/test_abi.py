@@ -81,6 +81,9 @@ def test_calls_on_a_null_plan_are_rejected(lib):
     assert lib.pisco_inject_mr_stall(None, 1000) == pisco.PISCO_EINVAL
     lib.pisco_plan_destroy(None)
     assert lib.pisco_plan_autotune(None, 0, 10, None, None, None, None, 1, None, None, None, None) == pisco.PISCO_EINVAL
+    off2 = (ctypes.c_int64 * 2)(0, 4)
+    assert lib.pisco_plan_autotune_batched(None, 1, off2, None, None, None, None, 1, None, None, None,
+                                           None) == pisco.PISCO_EINVAL
     z = (ctypes.c_double * 2)(0.0, 1.0)
     assert lib.pisco_convolve_psb(None, 0, 0, None, None, None, 2, z, None, None) == pisco.PISCO_EINVAL
     off = (ctypes.c_int64 * 2)(0, 4)

@@ -31,10 +31,11 @@ def test_clock_summary_without_samples():
     assert s == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
 
 
-def test_forward_traffic_is_reported_only_for_the_captured_launch_shape():
-    assert bench.FORWARD_TRAFFIC_BYTES.get((10_000_000, 16, 1)) == 486.63e6 + 47.03e6
-    assert bench.FORWARD_TRAFFIC_BYTES.get((500_000, 16, 1)) is None
-    assert bench.FORWARD_TRAFFIC_BYTES.get((10_000_000, 32, 1)) is None
+def test_forward_profile_figures_are_reported_only_for_the_captured_launch_shape():
+    rec = bench.FORWARD_PROFILE.get((10_000_000, 16, 1))
+    assert rec["traffic"] == 486.63e6 + 47.03e6 and rec["l1tex_pct"] == 93.1 and rec["lts_pct"] == 78.1
+    assert bench.FORWARD_PROFILE.get((500_000, 16, 1)) is None
+    assert bench.FORWARD_PROFILE.get((10_000_000, 32, 1)) is None
 
 
 def test_peaks_come_from_the_measured_file_else_the_fallback(tmp_path):

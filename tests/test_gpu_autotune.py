@@ -64,3 +64,41 @@ def test_autotune_refuses_plain_plans_and_bad_arguments():
         assert e.value.status == pisco.PISCO_EINVAL
         with pytest.raises(pisco.PiscoError):
             plan.autotune(th, ph, ps, det=3)
+
+
+def test_batched_autotune_tunes_every_detector_and_the_plan_uses_the_shape():
+    """A focal plane tuned on slices of all detectors' scans: the shape is one the kernel is built
+    for, the batched launch afterwards equals a fresh plan created with that shape (bit for bit),
+    and the detectors' TODs stay within the FP32 bound of the oracle."""
+    nside, r, n_det = 32, math.radians(8.0), 3
+    sky = sy.gaussian_sky(nside, 6).numpy()
+    grids = np.stack([sy.random_beam_maps(41, 60 + d) for d in range(n_det)])
+    dets = [(0.1 * d, 0.01 * d, 1.0) for d in range(n_det)]
+    lengths = [700, 1100, 400]
+    parts = [sy.ces_scan(m, offset=(0.03 * d, -0.02 * d)) for d, m in enumerate(lengths)]
+    th, ph, ps = (torch.cat([p[k] for p in parts]).numpy() for k in range(3))
+    offsets = [0] + list(np.cumsum(lengths))
+    sl = [np.arange(offsets[d], offsets[d] + 200) for d in range(n_det)]
+    sl_off = [0, 200, 400, 600]
+    ts, ps_, ss = (_t(np.concatenate([a[i] for i in sl])) for a in (th, ph, ps))
+    g = torch.as_tensor(grids, device=DEV).contiguous()
+    with pisco.Plan(nside, r, _t(sky), dets, g) as plan:
+        tile, npx, ms = plan.autotune_batched(sl_off, ts, ps_, ss, reps=2)
+        assert tile in (8, 16, 32) and npx in (1, 2) and ms > 0
+        tuned = plan.convolve_batched(offsets, _t(th), _t(ph), _t(ps))
+        plan.sync_status()
+        with pytest.raises(pisco.PiscoError) as e:
+            plan.autotune_batched([0, 5, 3], ts, ps_, ss)
+        assert e.value.status == pisco.PISCO_EINVAL
+    with pisco.Plan(nside, r, _t(sky), dets, g, tile_samples=tile, pixels_per_thread=npx) as fresh:
+        ref_shape = fresh.convolve_batched(offsets, _t(th), _t(ph), _t(ps))
+    torch.testing.assert_close(tuned, ref_shape, rtol=0, atol=0)
+    out = tuned.double().cpu().numpy()
+    for d in range(n_det):
+        idx = offsets[d] + np.array([0, lengths[d] // 2, lengths[d] - 1])
+        g64 = grids[d].astype(np.float64)
+        omega = ob.omega_tilde(g64[0], r)
+        ref = oc.tod(nside, r, sky, g64, dets[d], omega, th[idx], ph[idx], ps[idx])
+        for k, t in enumerate(idx):
+            pix, w = oc.sample_weights(nside, r, g64, dets[d], omega, th[t], ph[t], ps[t])
+            assert abs(out[t] - ref[k]) <= 2e-6 * np.sum(np.abs(w * sky[:, pix].T))
