@@ -283,7 +283,7 @@ def run_c1(args, dev):
         ms = _event_time(lambda: plan.convolve(th, ph, ps, out=tod), args.steps, args.warmup, stream)
     plan.sync_status()
     legs = {}
-    for name, fetch in (("packed_cells", pisco.PISCO_FETCH_PACKED),):
+    for name, fetch in (("packed_cells", pisco.PISCO_FETCH_PACKED), ("shared_nodes", pisco.PISCO_FETCH_SHARED)):
         with pisco.Plan(nside, r, sky, [det], g, beam_fetch=fetch, tile_samples=tuned[0],
                         pixels_per_thread=tuned[1]) as other:
             t_o = torch.empty(n, dtype=torch.float32, device=dev)

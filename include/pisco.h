@@ -89,7 +89,7 @@ typedef struct pisco_options {
     int precision;     /* PISCO_FP64_PLAIN or PISCO_FP32 */
     int tile_samples;       /* FP32 path: consecutive samples sharing one disc traversal: 8, 16 or 32 (0 = 16) */
     int pixels_per_thread;  /* FP32 path: consecutive ring pixels per thread: 1 or 2 (0 = 1) */
-    int beam_fetch;         /* FP32 path: PISCO_FETCH_CELLS, _TEXTURE or _PACKED (0 = cells) */
+    int beam_fetch;         /* FP32 path: PISCO_FETCH_CELLS, _TEXTURE, _PACKED or _SHARED (0 = cells) */
     int n_real;             /* PISCO_*_MR plans: realizations, a multiple of 32 in [32, 256] */
 } pisco_options;
 
@@ -101,8 +101,13 @@ typedef struct pisco_options {
  *                       power-of-two scale (each slope within 2^-15 of the largest
  *                       slope of its cell and map).  Half the bytes per pair of
  *                       the FP32 cells; the plan fails with PISCO_EINVAL when the
- *                       grid's slopes lie outside about 2^-80 .. 2^140. */
-enum { PISCO_FETCH_TEXTURE = 1, PISCO_FETCH_CELLS = 2, PISCO_FETCH_PACKED = 3 };
+ *                       grid's slopes lie outside about 2^-80 .. 2^140;
+ *  PISCO_FETCH_SHARED   the folded node grid (FP32 A, Bq', Cu' per node, 16 bytes)
+ *                       staged in shared memory once per block of a persistent
+ *                       launch (Sec. 5.2 keeps the beam in fast on-chip memory);
+ *                       grid_n <= 108, else PISCO_EINVAL; same arithmetic as the
+ *                       cells (bilinear in FP32 from the four nodes). */
+enum { PISCO_FETCH_TEXTURE = 1, PISCO_FETCH_CELLS = 2, PISCO_FETCH_PACKED = 3, PISCO_FETCH_SHARED = 4 };
 
 typedef struct pisco_plan pisco_plan;  /* opaque, owned by the library */
 
@@ -251,7 +256,7 @@ pisco_status pisco_convolve_batched(pisco_plan* plan, int n_det, const int64_t* 
  *           they replace detector det's own zeta.
  *   tod     device float32 [n_zeta][n] (row k = angle k); overwritten, NaN for
  *           invalid pointings as in pisco_convolve.
- * FP32 plans with PISCO_FETCH_CELLS only (PISCO_EUNSUPPORTED otherwise); the
+ * FP32 plans, any beam fetch but PISCO_FETCH_TEXTURE (PISCO_EUNSUPPORTED otherwise); the
  * pass runs the FP32 kernel with three accumulators per sample, so its
  * results agree with n_zeta pisco_convolve calls to FP32 rounding, not
  * bit for bit.  The paper computes each detector separately; this pass is an

@@ -207,9 +207,14 @@ extern "C" pisco_status pisco_plan_create(pisco_plan** out, int nside, double ra
     }
     int fetch = opt && opt->beam_fetch ? opt->beam_fetch : PISCO_FETCH_CELLS;
     if (mr) fetch = PISCO_FETCH_CELLS;  // the multi-realization kernel reads coefficient cells
-    if (fetch != PISCO_FETCH_TEXTURE && fetch != PISCO_FETCH_CELLS && fetch != PISCO_FETCH_PACKED) {
-        set_error(nullptr, "beam_fetch %d is not PISCO_FETCH_TEXTURE, PISCO_FETCH_CELLS or PISCO_FETCH_PACKED",
-                  fetch);
+    if (fetch != PISCO_FETCH_TEXTURE && fetch != PISCO_FETCH_CELLS && fetch != PISCO_FETCH_PACKED &&
+        fetch != PISCO_FETCH_SHARED) {
+        set_error(nullptr, "beam_fetch %d is not PISCO_FETCH_TEXTURE, _CELLS, _PACKED or _SHARED", fetch);
+        return PISCO_EINVAL;
+    }
+    if (fetch == PISCO_FETCH_SHARED && precision0 == PISCO_FP32 && grid_n > kSharedMaxGridN) {
+        set_error(nullptr, "grid_n %d exceeds %d, the largest node grid PISCO_FETCH_SHARED stages in shared memory",
+                  grid_n, kSharedMaxGridN);
         return PISCO_EINVAL;
     }
     if (!is_device_ptr(sky) || !is_device_ptr(beam_grids)) {
@@ -251,6 +256,7 @@ extern "C" pisco_status pisco_plan_create(pisco_plan** out, int nside, double ra
     else if (mr) p->beam_stride = nc * 4 * sizeof(float4);
     else if (fetch == PISCO_FETCH_CELLS) p->beam_stride = nc * 4 * sizeof(float4);
     else if (fetch == PISCO_FETCH_PACKED) p->beam_stride = (nc + 1) * 32;  // 32-byte header + cells
+    else if (fetch == PISCO_FETCH_SHARED) p->beam_stride = nn * sizeof(float4);  // folded nodes (A, Bq', Cu', 0)
     else p->beam_stride = 0;
     const size_t sky_bytes = mr ? (size_t)p->npix * 3 * n_real * 2
                              : precision == PISCO_FP32 ? p->npix * sizeof(float4) : 3 * p->npix * sizeof(double);
@@ -415,6 +421,8 @@ pisco_status pisco::run(pisco_plan* plan, int mode, int d0, int nd, const int64_
             e = launch_fast_cells(L, mode, plan->tile_samples, plan->pixels_per_thread, s);
         else if (plan->beam_fetch == PISCO_FETCH_PACKED)
             e = launch_fast_packed(L, mode, plan->tile_samples, plan->pixels_per_thread, s);
+        else if (plan->beam_fetch == PISCO_FETCH_SHARED)
+            e = launch_fast_shared(L, mode, plan->tile_samples, plan->pixels_per_thread, s);
         else e = launch_fast_texture(L, mode, plan->tile_samples, plan->pixels_per_thread, s);
         if (e != cudaSuccess) {
             set_error(plan, "kernel launch failed: %s", cudaGetErrorString(e));
@@ -496,7 +504,7 @@ extern "C" pisco_status pisco_convolve_psb(pisco_plan* plan, int det, int64_t n,
             return PISCO_EINVAL;
         }
     if (plan->precision != PISCO_FP32 || plan->beam_fetch == PISCO_FETCH_TEXTURE) {
-        set_error(plan, "pisco_convolve_psb needs an FP32 plan with PISCO_FETCH_CELLS or PISCO_FETCH_PACKED");
+        set_error(plan, "pisco_convolve_psb needs an FP32 plan whose beam fetch is not PISCO_FETCH_TEXTURE");
         return PISCO_EUNSUPPORTED;
     }
     pisco_status st = check_pointing(plan, n, theta, phi, psi);

@@ -24,9 +24,10 @@
 //     orthographic grid coordinates (u, v) = (x, y) (Sec. 4.2), either from
 //     64-byte coefficient cells read through L1/L2 (one 32-byte and one
 //     16-byte load), from 32-byte packed cells (FP32 values, int16 slopes on
-//     a per-cell power-of-two scale; one 32-byte load) or from 2 x 2 texel
+//     a per-cell power-of-two scale; one 32-byte load), from 2 x 2 texel
 //     gathers of the node maps through the texture path (grids of 100s of KB
-//     to MB, read at scattered cells);
+//     to MB, read at scattered cells), or from the four nodes of the cell in
+//     shared memory (node grids up to 108^2, staged once per block);
 //  6. the Ludwig-3 angle (Appendix A) enters through
 //        e^{2 i chi} = e^{2 i zeta} (-e1 + i e2)^2 / sin^2(theta_k),
 //        e1 = Z_theta - x (Z_p + m), e2 = Z_phi - y (Z_p + m),
@@ -137,9 +138,15 @@ static __device__ __forceinline__ float hi16(unsigned w) { return (float)((int)w
 // the shared-geometry pass keeps three accumulators per sample and is fastest at
 // 2; the beam-grid transpose, bound by its atomic adds, at 4.
 constexpr int fast_min_blocks(int mode) { return mode == kPsb ? 2 : (mode == kGrid ? 4 : 3); }
+// Threads per block: NT, or for the shared-memory fetch (one block per SM, its shared memory
+// holding the node grid) three times as many, the same 24 warps per SM.
+constexpr int fast_threads(int fetch) { return fetch == PISCO_FETCH_SHARED ? 3 * NT : NT; }
+constexpr int fast_blocks(int fetch, int mode) { return fetch == PISCO_FETCH_SHARED ? 1 : fast_min_blocks(mode); }
 
 template <int S, int NP, int FETCH, int MODE>
-__global__ void __launch_bounds__(NT, fast_min_blocks(MODE)) k_fast(const __grid_constant__ LaunchParams P) {
+__global__ void __launch_bounds__(fast_threads(FETCH), fast_blocks(FETCH, MODE))
+    k_fast(const __grid_constant__ LaunchParams P) {
+    constexpr int NTK = fast_threads(FETCH), NWK = NTK / 32;
     __shared__ double sTh[S], sPh[S], sPx[S], sPy[S], sPz[S];
     __shared__ float4 sA[S];  // cos(b/2), sin(b/2), cos psi0, sin psi0   (b = phi0 - phi_c)
     __shared__ float4 sB[S];  // cos theta0, sin theta0, Z_theta, Z_phi
@@ -155,7 +162,11 @@ __global__ void __launch_bounds__(NT, fast_min_blocks(MODE)) k_fast(const __grid
     __shared__ int sFlag[RC];
     __shared__ int sJlo[RC], sJref[RC], sFirst[RC], sRc[RC], sCnt[RC], sPref[RC + 1], sWarpTot[RC / 32];
     __shared__ float sAref[RC], sSr[RC], sInv[RC], sDph[RC];
-    __shared__ float sRed[NW][S];
+    __shared__ float sRed[NWK][S];
+
+    // shared-memory fetch: the folded node grid of the current detector, [N][N] (A, Bq', Cu', 0)
+    extern __shared__ float4 sGridNodes[];
+    int grid_det = -1;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const float4* __restrict__ sky = (const float4*)P.sky;
@@ -174,6 +185,14 @@ __global__ void __launch_bounds__(NT, fast_min_blocks(MODE)) k_fast(const __grid
         const float* __restrict__ cells = (const float*)det.beam;
         // packed cells: biased exponent of the unit slope scale, from the 32-byte header
         const int qbase = FETCH == PISCO_FETCH_PACKED ? __ldg((const int*)det.beam) : 0;
+        if (FETCH == PISCO_FETCH_SHARED && d != grid_det) {
+            // stage this detector's node grid (once per block and detector of the persistent launch)
+            __syncthreads();
+            const float4* __restrict__ src = (const float4*)det.beam;
+            for (int q = tid; q < P.grid_n * P.grid_n; q += NTK) sGridNodes[q] = __ldg(src + q);
+            __syncthreads();
+            grid_det = d;
+        }
 
         // 1. per-sample constants
         if (tid < S) {
@@ -282,7 +301,7 @@ __global__ void __launch_bounds__(NT, fast_min_blocks(MODE)) k_fast(const __grid
                 const int nr = min(RC, rhi - c0 + 1);
 
                 // 3. per (ring, sample) offsets and the union of the discs' longitude ranges
-                for (int item = tid; item < RC * S; item += NT) {
+                for (int item = tid; item < RC * S; item += NTK) {
                     const int ri = item / S, i = item % S;
                     float lo = __int_as_float(0x7f800000), hi = -__int_as_float(0x7f800000);
                     int full = 0;
@@ -384,7 +403,7 @@ __global__ void __launch_bounds__(NT, fast_min_blocks(MODE)) k_fast(const __grid
                 // 4-7. runs of NP pixels x samples of the group: every per-sample value
                 // read from shared memory serves NP pairs from registers
                 const int totalq = sPref[nr];
-                for (int qd = tid; qd < totalq; qd += NT) {
+                for (int qd = tid; qd < totalq; qd += NTK) {
                     int lo_ = 0, hi_ = nr - 1;
                     while (lo_ < hi_) {
                         const int mid = (lo_ + hi_ + 1) >> 1;
@@ -525,6 +544,17 @@ __global__ void __launch_bounds__(NT, fast_min_blocks(MODE)) k_fast(const __grid
                                 bA = fmaf(sA, fmaf(fy, fmaf(fx, lo16(w4), hi16(w3)), fx * lo16(w3)), lo.x);
                                 bB = fmaf(sB, fmaf(fy, fmaf(fx, hi16(w5), lo16(w5)), fx * hi16(w4)), lo.y);
                                 bC = fmaf(sC, fmaf(fy, fmaf(fx, lo16(w7), hi16(w6)), fx * lo16(w6)), lo.z);
+                            } else if (FETCH == PISCO_FETCH_SHARED) {
+                                // bilinear in FP32 from the cell's four nodes in shared memory
+                                const int q00 = (int)flv * P.grid_n + (int)flu;
+                                const float4 n00 = sGridNodes[q00], n10 = sGridNodes[q00 + 1];
+                                const float4 n01 = sGridNodes[q00 + P.grid_n], n11 = sGridNodes[q00 + P.grid_n + 1];
+                                const float ax = fmaf(fx, n10.x - n00.x, n00.x), bx = fmaf(fx, n11.x - n01.x, n01.x);
+                                const float ay = fmaf(fx, n10.y - n00.y, n00.y), by = fmaf(fx, n11.y - n01.y, n01.y);
+                                const float az = fmaf(fx, n10.z - n00.z, n00.z), bz = fmaf(fx, n11.z - n01.z, n01.z);
+                                bA = fmaf(fy, bx - ax, ax);
+                                bB = fmaf(fy, by - ay, ay);
+                                bC = fmaf(fy, bz - az, az);
                             } else {
                                 // texel centres sit at integer + 1/2: (flu + 1, flv + 1) selects
                                 // nodes flu, flu + 1 and flv, flv + 1 exactly
@@ -591,7 +621,7 @@ __global__ void __launch_bounds__(NT, fast_min_blocks(MODE)) k_fast(const __grid
                 if (tid >= gs && tid < ge && sValid[tid]) {
                     double s = 0.0;
 #pragma unroll
-                    for (int w = 0; w < NW; ++w) s += (double)sRed[w][tid];
+                    for (int w = 0; w < NWK; ++w) s += (double)sRed[w][tid];
                     if (MODE == kForward) ((float*)P.out)[t0 + tid] = (float)(det.scale * s);
                     else P.counts[t0 + tid] = (int32_t)s;
                 }
@@ -611,7 +641,7 @@ __global__ void __launch_bounds__(NT, fast_min_blocks(MODE)) k_fast(const __grid
                     }
                     __syncthreads();
                     if (tid >= gs && tid < ge && sValid[tid])
-                        for (int w = 0; w < NW; ++w) part[c] += (double)sRed[w][tid];
+                        for (int w = 0; w < NWK; ++w) part[c] += (double)sRed[w][tid];
                     __syncthreads();
                 }
                 if (tid >= gs && tid < ge && sValid[tid]) {
@@ -633,26 +663,45 @@ __global__ void __launch_bounds__(NT, fast_min_blocks(MODE)) k_fast(const __grid
     }
 }
 
+// One launch of mode MODE: a grid of one block per tile, or, for the shared-memory fetch, a
+// persistent grid of the resident blocks (each stages the node grid once).
+template <int S, int NP, int FETCH, int MODE>
+static cudaError_t launch_mode(const LaunchParams& p, cudaStream_t s) {
+    unsigned grid = (unsigned)min(p.total_tiles, (long long)INT_MAX);
+    size_t dyn = 0;
+    if constexpr (FETCH == PISCO_FETCH_SHARED) {
+        dyn = (size_t)p.grid_n * p.grid_n * sizeof(float4);
+        cudaError_t e = cudaFuncSetAttribute(k_fast<S, NP, FETCH, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)dyn);
+        if (e != cudaSuccess) return e;
+        int dev = 0, n_sm = 0, per_sm = 0;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fast<S, NP, FETCH, MODE>, fast_threads(FETCH), dyn);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;
+        grid = (unsigned)min((long long)grid, (long long)n_sm * per_sm);
+    }
+    k_fast<S, NP, FETCH, MODE><<<grid, fast_threads(FETCH), dyn, s>>>(p);
+    return cudaGetLastError();
+}
+
 template <int S, int NP, int FETCH>
 static cudaError_t launch_s(const LaunchParams& p, int mode, cudaStream_t s) {
     if (p.total_tiles <= 0) return cudaSuccess;
-    const unsigned grid = (unsigned)min(p.total_tiles, (long long)INT_MAX);
     if (mode == kPsb) {
         // three accumulators per sample: instantiated for beam cells only
-        if constexpr (FETCH != PISCO_FETCH_TEXTURE) {
-            k_fast<S, NP, FETCH, kPsb><<<grid, NT, 0, s>>>(p);
-            return cudaGetLastError();
-        }
+        if constexpr (FETCH != PISCO_FETCH_TEXTURE) return launch_mode<S, NP, FETCH, kPsb>(p, s);
         return cudaErrorInvalidValue;
     }
     switch (mode) {
-        case kForward: k_fast<S, NP, FETCH, kForward><<<grid, NT, 0, s>>>(p); break;
-        case kAdjoint: k_fast<S, NP, FETCH, kAdjoint><<<grid, NT, 0, s>>>(p); break;
-        case kGrid: k_fast<S, NP, FETCH, kGrid><<<grid, NT, 0, s>>>(p); break;
-        case kBoth: k_fast<S, NP, FETCH, kBoth><<<grid, NT, 0, s>>>(p); break;
-        default: k_fast<S, NP, FETCH, kCount><<<grid, NT, 0, s>>>(p); break;
+        case kForward: return launch_mode<S, NP, FETCH, kForward>(p, s);
+        case kAdjoint: return launch_mode<S, NP, FETCH, kAdjoint>(p, s);
+        case kGrid: return launch_mode<S, NP, FETCH, kGrid>(p, s);
+        case kBoth: return launch_mode<S, NP, FETCH, kBoth>(p, s);
+        default: return launch_mode<S, NP, FETCH, kCount>(p, s);
     }
-    return cudaGetLastError();
 }
 
 // Dispatch over the tile size and pixels per thread for one fetch mode.

@@ -91,7 +91,7 @@ struct pisco_plan {
     int precision;
     int tile_samples;
     int pixels_per_thread;
-    int beam_fetch;    // PISCO_FETCH_CELLS or PISCO_FETCH_TEXTURE
+    int beam_fetch;    // PISCO_FETCH_CELLS, _TEXTURE, _PACKED or _SHARED
     int n_real;        // realizations (multi-realization plans), else 1
     double radius;
     double cos_r;
@@ -146,6 +146,9 @@ inline size_t folded_coef_grad_bytes(int grid_n) { return (size_t)(grid_n - 1) *
 cudaError_t launch_fast_texture(const LaunchParams& p, int mode, int tile_samples, int np, cudaStream_t s);
 cudaError_t launch_fast_cells(const LaunchParams& p, int mode, int tile_samples, int np, cudaStream_t s);
 cudaError_t launch_fast_packed(const LaunchParams& p, int mode, int tile_samples, int np, cudaStream_t s);
+cudaError_t launch_fast_shared(const LaunchParams& p, int mode, int tile_samples, int np, cudaStream_t s);
+// Largest node grid the shared-memory fetch stages (16 bytes per node; 182 KB at 108 nodes).
+constexpr int kSharedMaxGridN = 108;
 cudaError_t launch_plain(const LaunchParams& p, int mode, cudaStream_t s);
 cudaError_t launch_mr(const LaunchParams& p, int f16, cudaStream_t s);
 cudaError_t launch_plan_kernels(pisco_plan* plan, const void* sky, int sky_dtype,

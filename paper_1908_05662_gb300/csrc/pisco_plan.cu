@@ -210,6 +210,17 @@ __global__ void k_nodes32(const float* __restrict__ g, int n, double eps, double
     out[2 * nn + idx] = (float)f.c;
 }
 
+// Folded node values as one float4 (A, Bq', Cu', 0) per node, for the shared-memory fetch.
+__global__ void k_nodes4(const float* __restrict__ g, int n, double eps, double zeta, float4* __restrict__ out) {
+    const long long nn = (long long)n * n;
+    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= nn) return;
+    double s2z, c2z;
+    sincos(2.0 * zeta, &s2z, &c2z);
+    Folded f = fold_node(g, nn, idx, eps, c2z, s2z);
+    out[idx] = make_float4((float)f.a, (float)f.b, (float)f.c, 0.f);
+}
+
 // One block; fixed per-thread order and a fixed tree, so the result is deterministic.
 __global__ void k_omega(const float* __restrict__ tt, int n, double sin_r, double* out) {
     __shared__ double red[256];
@@ -374,6 +385,8 @@ cudaError_t launch_beam_kernels(pisco_plan* plan, const float* grids, cudaStream
             const long long nc = (long long)(n - 1) * (n - 1);
             if (plan->beam_fetch == PISCO_FETCH_CELLS) {
                 k_cells<<<blocks_for(nc, 256), 256, 0, s>>>(g, n, det.eps, det.zeta, (float4*)dst);
+            } else if (plan->beam_fetch == PISCO_FETCH_SHARED) {
+                k_nodes4<<<blocks_for(nn, 256), 256, 0, s>>>(g, n, det.eps, det.zeta, (float4*)dst);
             } else if (plan->beam_fetch == PISCO_FETCH_PACKED) {
                 cudaError_t e = cudaMemsetAsync(dst, 0, 32, s);
                 if (e != cudaSuccess) return e;

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libpisco.so
 PISCO_OK, PISCO_EINVAL, PISCO_ENOMEM, PISCO_ECUDA, PISCO_ETIMEOUT, PISCO_EUNSUPPORTED, PISCO_EDEVICE = range(7)
 PISCO_FP64_PLAIN, PISCO_FP32, PISCO_BF16_MR, PISCO_FP16_MR = 0, 1, 2, 3
 PISCO_DTYPE_F32, PISCO_DTYPE_F64, PISCO_DTYPE_BF16, PISCO_DTYPE_F16 = 0, 1, 2, 3
-PISCO_FETCH_TEXTURE, PISCO_FETCH_CELLS, PISCO_FETCH_PACKED = 1, 2, 3
+PISCO_FETCH_TEXTURE, PISCO_FETCH_CELLS, PISCO_FETCH_PACKED, PISCO_FETCH_SHARED = 1, 2, 3, 4
 
 STATUS_NAMES = {0: "PISCO_OK", 1: "PISCO_EINVAL", 2: "PISCO_ENOMEM", 3: "PISCO_ECUDA",
                 4: "PISCO_ETIMEOUT", 5: "PISCO_EUNSUPPORTED", 6: "PISCO_EDEVICE"}
