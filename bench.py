@@ -879,7 +879,7 @@ def main():
     h = [x.cpu().pin_memory() for x in (th, ph, ps)]
     h_tod = torch.empty(n, dtype=torch.float32).pin_memory()
     plan.convolve_host(*h, out=h_tod)
-    e2e_steps = 2
+    e2e_steps = max(args.steps, 3)
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         plan.convolve_host(*h, out=h_tod)
@@ -937,7 +937,8 @@ def main():
                          "kernel": f"pisco::k_fast<{tuned[0]}, {tuned[1]}, cells, forward>",
                          "peak_note": "FP32 from unit counts: 152 SM x 128 lanes x 2 x 2070 MHz",
                          "hbm_frac": (28 * n / (ms / 1e3)) / (HBM_GBS * 1e9), "hbm_peak_source": PEAK_SOURCE},
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 24 * n, "d2h_bytes_per_step": 4 * n},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 24 * n, "d2h_bytes_per_step": 4 * n,
+                    "steps": e2e_steps},
             "plain_fp64_gpu": {"value": plain_rate * world, "unit": UNIT, "samples_timed": n_plain,
                                "speedup_of_fp32": value / (plain_rate * world),
                                "fp32_vs_fp64_normwise": fp32_vs_64},

@@ -366,8 +366,10 @@ __global__ void __launch_bounds__(MT, 1) k_mr(const __grid_constant__ LaunchPara
         const bool sched = warp == 1;
         const int pt = tid - 64;                   // producer thread index (producers only)
         const int pw = pt >> 5;                    // producer warp 0 .. 15
-        const int my_t = 8 * pw + (lane & 7);      // producer: its sample in the tile
-        const int my_q = lane >> 3;                // producer: its pixel quad (block my_q >> 1)
+        // producer: its sample and pixel quad (block my_q >> 1); a warp takes 32 consecutive
+        // samples of one quad, whose pairs mostly fall inside (or outside) the disc together
+        const int my_t = 32 * (pw & 3) + lane;
+        const int my_q = pw >> 2;
         const int nc = P.grid_n - 1;
         const float gmax = (float)(P.grid_n - 2);
         const double wr = P.mr_wr;  // 1 - cos R
@@ -386,6 +388,9 @@ __global__ void __launch_bounds__(MT, 1) k_mr(const __grid_constant__ LaunchPara
             const int ns = (int)min((long long)MS, det.count - lt * MS);
             const float* __restrict__ cells = (const float*)det.beam;
 
+            // every producer has finished the previous tile's epilogue (its reads of sValid)
+            // before the per-sample data are rewritten
+            named_sync();
             // 1. per-sample constants (FP64 basis, FP32 copies)
             if (!sched && pt < MS) {
                 const int i = pt;
@@ -793,7 +798,7 @@ __global__ void __launch_bounds__(MT, 1) k_mr(const __grid_constant__ LaunchPara
                         // the A operand rows: map m, part hi / lo, 8 bytes at core matrix
                         // (my_t / 8, 2 m + b), row my_t % 8, bytes 8 (my_q % 2) ..
                         unsigned char* st = dyn + s * sbytes;
-                        const int off = pw * A_SBO + b * A_LBO + (my_t & 7) * 16 + (my_q & 1) * 8;
+                        const int off = (my_t >> 3) * A_SBO + b * A_LBO + (my_t & 7) * 16 + (my_q & 1) * 8;
 #pragma unroll
                         for (int m = 0; m < 3; ++m) {
                             uint2 hi, lo;
