@@ -16,10 +16,12 @@
 // batch is two such blocks.  The contraction index of a batch is map-major,
 // k = 16 m + p (m = I, Q, U; p = pixel of the batch), so that
 //   * the realization rows of one block, [8 pixels][I, Q, U][R] in the stack,
-//     land by one 4-D TMA tile load as the B operand's core matrices
-//     (MN-major, no swizzle: [R/8][3 maps][8 pixels][8 realizations]);
+//     land by one 4-D TMA tile load as the B operand in the MN-major layout
+//     with 64-byte swizzling: atoms of 8 pixels x 32 realizations (rows of
+//     64 bytes), ordered [R/32][3 maps][8 pixels][32 realizations], so the
+//     copy engine moves 64-byte rows (192 per block at R = 256);
 //   * a thread's four weights of one map are one 8-byte row segment of the A
-//     operand's K-major core matrices.
+//     operand's K-major core matrices (no swizzling).
 //
 // Warp roles (576 threads):
 //   warp 0      one thread issues the MMAs: per batch, for the three maps,
@@ -78,16 +80,17 @@ constexpr int NPT = 32 * NPW;             // producer threads
 constexpr int MRC = 32;                   // rings per chunk of the union
 constexpr int KPIX = 16;                  // union pixels per batch (two blocks of 8)
 constexpr int KB = 3 * KPIX;              // contraction length per batch (3 K-steps of 16)
-constexpr int NST = 4;                    // pipeline stages
-static_assert((NST & (NST - 1)) == 0, "NST is a power of two");
+constexpr int NST = 3;                    // pipeline stages (3 leave L1 room for the beam cells)
 constexpr int WINB = NPT / 16;            // batches per pixel-table window (one pixel per producer thread)
 constexpr int MAXR = 256;                 // realizations (MMA N) at most
 // A operand (weights, K-major): core matrix (t / 8, k / 8), 8 rows of 16 bytes
 constexpr int A_LBO = 128;                // bytes between core matrices adjacent in K
 constexpr int A_SBO = (KB / 8) * 128;     // bytes between core matrices adjacent in M (768)
 constexpr int A_BYTES = MS * KB * 2;      // one 16-bit weight part of a batch (12 KB)
-// B operand (realizations, MN-major): per block [R/8][3 maps][8 pixels][8 realizations]
-constexpr int B_SBO = 3 * 128;            // bytes between core matrices adjacent in N
+// B operand (realizations, MN-major, 64-byte swizzle): per block [R/32][3 maps][8 pixels][32 realizations]
+constexpr int B_ATOM = 8 * 64;            // one swizzle atom: 8 pixels (K) x 32 realizations (N)
+constexpr int B_LBO = 3 * B_ATOM;         // bytes between atoms adjacent in N
+constexpr unsigned kSwizzle64 = 4u;       // descriptor layout type: 64-byte swizzling
 __host__ __device__ constexpr int block_bytes(int nreal) { return 48 * nreal; }  // K-adjacent core matrices
 __host__ __device__ constexpr int stage_bytes(int nreal) { return 2 * A_BYTES + 2 * block_bytes(nreal); }
 constexpr int BAR_ID = 1;                 // named barrier of the scheduler and the producers
@@ -156,11 +159,16 @@ __device__ __forceinline__ void named_sync() {
 }
 
 // Shared-memory matrix descriptor of the fifth-generation MMA: start address,
-// leading (K-direction) and stride (M/N-direction) byte offsets between core
-// matrices, descriptor version 1, no swizzle.
-__device__ __forceinline__ unsigned long long smem_desc(unsigned addr, unsigned lbo, unsigned sbo) {
+// leading and stride byte offsets, descriptor version 1, layout type (bits
+// 61-63).  Without swizzling the leading offset steps between core matrices
+// along K and the stride offset along M/N; in a swizzled MN-major layout the
+// leading offset steps between atoms along N and the stride offset between
+// groups of 8 rows along K.
+__device__ __forceinline__ unsigned long long smem_desc(unsigned addr, unsigned lbo, unsigned sbo,
+                                                        unsigned layout = 0u) {
     return (unsigned long long)((addr >> 4) & 0x3FFFu) | ((unsigned long long)((lbo >> 4) & 0x3FFFu) << 16) |
-           ((unsigned long long)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+           ((unsigned long long)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46) |
+           ((unsigned long long)layout << 61);
 }
 
 // Instruction descriptor, kind::f16: FP32 accumulate, A and B both BF16 (or
@@ -186,7 +194,9 @@ __device__ __forceinline__ void mma_commit(unsigned long long* bar) {
 }
 
 // TMA tile load of the 4-D realization tensor's box at (0, pix, 0, 0) into dst
-// (128-byte aligned); completes `bar`'s transaction count by the box's bytes.
+// (512-byte aligned, the period of the 64-byte swizzle, which the copy engine
+// and the MMA both take from the shared-memory address); completes `bar`'s
+// transaction count by the box's bytes.
 __device__ __forceinline__ void tma_tile4(void* dst, const CUtensorMap* map, int pix, unsigned long long* bar) {
     asm volatile(
         "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
@@ -195,12 +205,14 @@ __device__ __forceinline__ void tma_tile4(void* dst, const CUtensorMap* map, int
         : "memory");
 }
 
-// 64-byte beam cell: one 32-byte and one 16-byte read-only load, not allocated in L1.
+// 64-byte beam cell: one 32-byte and one 16-byte read-only load, cached in L1 (a
+// lane's next pixel of the ring often falls in the cell a later sample of its
+// warp has just read).
 __device__ __forceinline__ void ld_cell(const float* p, float4& a, float4& b, float4& c) {
-    asm("ld.global.nc.L1::no_allocate.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+    asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
         : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
         : "l"(p));
-    asm("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
+    asm("ld.global.nc.v4.f32 {%0,%1,%2,%3}, [%4];"
         : "=f"(c.x), "=f"(c.y), "=f"(c.z), "=f"(c.w)
         : "l"(p + 8));
 }
@@ -239,8 +251,8 @@ __device__ __forceinline__ void split4(const float v[4], uint2& hi, uint2& lo) {
 }  // namespace
 
 // `rows` is the realization stack seen as a 4-D tensor of 16-bit values: element
-// (c, p, m, q) = realization 8 q + c of map m of pixel p, with a box of 8 x 8 x 3 x R/8
-// whose shared-memory image [q][m][8 pixels][8] is one block's core matrices.
+// (c, p, m, q) = realization 32 q + c of map m of pixel p, with a box of 32 x 8 x 3 x R/32
+// whose shared-memory image [q][m][8 pixels][32], 64-byte swizzled, is one block's atoms.
 template <int F16>
 __global__ void __launch_bounds__(MT, 1) k_mr(const __grid_constant__ LaunchParams P,
                                               const __grid_constant__ CUtensorMap rows) {
@@ -340,7 +352,7 @@ __global__ void __launch_bounds__(MT, 1) k_mr(const __grid_constant__ LaunchPara
                 const unsigned ah = smem_u32(st), al = smem_u32(st + A_BYTES), bb = smem_u32(st + 2 * A_BYTES);
 #pragma unroll
                 for (int m = 0; m < 3; ++m) {
-                    const unsigned long long bd = smem_desc(bb + m * 128, (unsigned)bbytes, B_SBO);
+                    const unsigned long long bd = smem_desc(bb + m * B_ATOM, B_LBO, (unsigned)bbytes, kSwizzle64);
                     const unsigned acc = (first && m == 0) ? 0u : 1u;
                     mma_f16(tmem, smem_desc(ah + m * 2 * A_LBO, A_LBO, A_SBO), bd, idesc, acc);
                     mma_f16(tmem + ncols, smem_desc(al + m * 2 * A_LBO, A_LBO, A_SBO), bd, idesc, acc);
@@ -922,14 +934,15 @@ cudaError_t launch_mr(const LaunchParams& p0, int f16, cudaStream_t s) {
     const EncodeTiled encode = encode_tiled();
     if (!encode || p.npix >= INT_MAX || p.n_real % 32 != 0 || p.n_real < 32 || p.n_real > MAXR)
         return cudaErrorInvalidValue;
-    // the stack [Npix][3][R] of 16-bit values as (8 realizations, pixel, map, R / 8 groups): innermost
-    // box extent 16 bytes, every box starts at realization 0 of its pixel (16-byte aligned)
+    // the stack [Npix][3][R] of 16-bit values as (32 realizations, pixel, map, R / 32 groups): innermost
+    // box extent 64 bytes (the 64-byte swizzle span), every box starts at realization 0 of its pixel
+    // (16-byte aligned); the shared-memory destinations are 1024-byte aligned
     CUtensorMap rows;
-    const cuuint64_t dims[4] = {8, (cuuint64_t)p.npix, 3, (cuuint64_t)(p.n_real / 8)};
-    const cuuint64_t strides[3] = {(cuuint64_t)p.n_real * 6, (cuuint64_t)p.n_real * 2, 16};
-    const cuuint32_t box[4] = {8, 8, 3, (cuuint32_t)(p.n_real / 8)}, estr[4] = {1, 1, 1, 1};
+    const cuuint64_t dims[4] = {32, (cuuint64_t)p.npix, 3, (cuuint64_t)(p.n_real / 32)};
+    const cuuint64_t strides[3] = {(cuuint64_t)p.n_real * 6, (cuuint64_t)p.n_real * 2, 64};
+    const cuuint32_t box[4] = {32, 8, 3, (cuuint32_t)(p.n_real / 32)}, estr[4] = {1, 1, 1, 1};
     if (encode(&rows, CU_TENSOR_MAP_DATA_TYPE_UINT16, 4, const_cast<void*>(p.sky), dims, strides, box, estr,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
     static int n_sm = 0;
