@@ -23,31 +23,38 @@
 //   * a thread's four weights of one map are one 8-byte row segment of the A
 //     operand's K-major core matrices (no swizzling).
 //
-// Warp roles (576 threads):
+// Warp roles (640 threads):
 //   warp 0      one thread issues the MMAs: per batch, for the three maps,
 //               W_hi x S and W_lo x S (kind::f16) into two FP32 accumulators in
 //               TMEM (2 x R columns; the epilogue adds them),
 //               then tcgen05.commit to the stage's "empty" barrier, and at the
 //               tile's end to the accumulator's "full" barrier;
-//   warp 1      the scheduler: per batch, the pixel table (ring, in-ring index,
-//               half-angle of the longitude offset), the two TMA loads of the
-//               realization rows, and the stage's control word;
-//   warps 2-17  the weight producers: thread (sample t, pixel quad q) computes
+//   warp 1      the scheduler: per batch, the stage's control word and the two
+//               TMA loads of the realization rows;
+//   warps 2-3   the planner, one tile and up to two windows ahead of the
+//               others: per tile the samples' constants (FP64 basis, FP32
+//               copies), per chunk of 32 rings the union of the tile's discs
+//               (a longitude range per ring, cut into blocks of 8 pixels), per
+//               window of 32 batches the pixel table (ring, in-ring index,
+//               half-angle of the longitude offset);
+//   warps 4-19  the weight producers: thread (sample t, pixel quad q) computes
 //               the FP32 weights of 4 pairs (geometry, 64-byte beam cell, the
 //               Ludwig-3 rotation), splits each into two 16-bit parts
 //               W = W_hi + W_lo (W_lo the rounded remainder) and stores them;
 //               at a tile's end they read the accumulator back (tcgen05.ld)
 //               and write d[t][r] = scale * D[t][r].
-// A ring of NST stages (operand buffers + pixel table + control word) links
-// them through mbarriers: "pixels" (scheduler -> producers), "loads" (TMA
-// bytes + scheduler -> MMA), "full" (16 producer warps -> MMA), "empty" (MMA
-// commit -> scheduler and producers).  The scheduler and the producers meet
-// at a named barrier only where a tile or a chunk of 32 rings begins.
+// mbarriers link them: a ring of NST operand stages ("loads": TMA bytes +
+// scheduler -> MMA; "full": 16 producer warps -> MMA; "empty": MMA commit ->
+// scheduler and producers), two window buffers ("window full": planner ->
+// scheduler and producers; "window empty": back), two tile buffers of
+// per-sample data ("tile free": producers after their epilogue -> planner)
+// and the accumulator ("full": MMA -> producers; "empty": back).  No role
+// waits on a CTA-wide barrier between the prologue and the end.
 //
 // Precision of the disc decision.  The FP32 offsets of a pair come from the
 // half-angles of the pixel's and the sample's longitudes relative to the
 // tile's reference; their absolute error grows with those angles.  Per chunk
-// the scheduler bounds the resulting relative error of 1 - k . p0 from the
+// the planner bounds the resulting relative error of 1 - k . p0 from the
 // largest half-angles of the chunk's pixels and the tile's samples; where the
 // bound exceeds the kernel's FP64 re-decision band (2e-5 relative; tiles whose
 // samples lie far apart, which scans do not produce) the chunk takes the half-angles in FP64
@@ -75,13 +82,15 @@ namespace {
 
 constexpr int MS = 128;                   // samples per tile = MMA M
 constexpr int NPW = 16;                   // weight-producer warps
-constexpr int MT = 32 * (2 + NPW);        // threads: MMA warp, scheduler warp, producers
-constexpr int NPT = 32 * NPW;             // producer threads
+constexpr int NRW = 4;                    // role warps: MMA issuer, scheduler, two planner warps
+constexpr int MT = 32 * (NRW + NPW);      // threads
 constexpr int MRC = 32;                   // rings per chunk of the union
 constexpr int KPIX = 16;                  // union pixels per batch (two blocks of 8)
 constexpr int KB = 3 * KPIX;              // contraction length per batch (3 K-steps of 16)
 constexpr int NST = 3;                    // pipeline stages (3 leave L1 room for the beam cells)
-constexpr int WINB = NPT / 16;            // batches per pixel-table window (one pixel per producer thread)
+constexpr int WINB = 32;                  // batches per window of the pixel table
+constexpr int WPIX = 16 * WINB;           // pixels per window
+constexpr int WBLK = 2 * WINB;            // blocks of 8 pixels per window
 constexpr int MAXR = 256;                 // realizations (MMA N) at most
 // A operand (weights, K-major): core matrix (t / 8, k / 8), 8 rows of 16 bytes
 constexpr int A_LBO = 128;                // bytes between core matrices adjacent in K
@@ -93,9 +102,19 @@ constexpr int B_LBO = 3 * B_ATOM;         // bytes between atoms adjacent in N
 constexpr unsigned kSwizzle64 = 4u;       // descriptor layout type: 64-byte swizzling
 __host__ __device__ constexpr int block_bytes(int nreal) { return 48 * nreal; }  // K-adjacent core matrices
 __host__ __device__ constexpr int stage_bytes(int nreal) { return 2 * A_BYTES + 2 * block_bytes(nreal); }
-constexpr int BAR_ID = 1;                 // named barrier of the scheduler and the producers
-constexpr int BAR_N = 32 * (1 + NPW);
-enum { CT_FIRST = 1, CT_LAST = 2, CT_END = 4 };
+enum { CT_FIRST = 1, CT_LAST = 2, CT_END = 4 };            // stage control word
+enum { W_TFIRST = 1, W_TLAST = 2, W_END = 4 };             // window flags: a tile's first / last window
+struct WinMeta {
+    int nb;       // batches in the window
+    int precise;  // the chunk takes the double-FP32 longitude offsets
+    int flags;
+    int tb;       // the tile buffer of its per-sample data
+};
+struct TileMeta {
+    long long t0;  // first sample of the tile
+    int ns;        // samples in the tile
+    int d;         // detector
+};
 constexpr float kEps32 = 5.9604645e-8f;   // FP32 unit roundoff
 constexpr double kBand = 2e-5;            // relative half-width of the FP64 re-decision band (the
                                           // launcher sets the band edges from it)
@@ -154,8 +173,23 @@ __device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned
                  : "memory");
 }
 
-__device__ __forceinline__ void named_sync() {
-    asm volatile("bar.sync %0, %1;" ::"r"(BAR_ID), "r"(BAR_N) : "memory");
+// The block's failure flag as lane 0 of the warp sees it (a warp-uniform value).
+__device__ __forceinline__ bool warp_failed(volatile int* failed) {
+    return __shfl_sync(0xffffffffu, *failed, 0) != 0;
+}
+
+// The planner's two warps meet at named barrier 1.
+__device__ __forceinline__ void plan_sync() { asm volatile("bar.sync 1, 64;" ::: "memory"); }
+
+// mbar_wait by lane 0 of a warp, the outcome broadcast to the warp (whose later reads are
+// ordered after lane 0's).
+__device__ __forceinline__ bool warp_wait(unsigned long long* bar, unsigned parity, volatile int* failed,
+                                          long long limit, int* err) {
+    bool ok = true;
+    if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, failed, limit, err);
+    ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+    __syncwarp();
+    return ok;
 }
 
 // Shared-memory matrix descriptor of the fifth-generation MMA: start address,
@@ -256,34 +290,37 @@ __device__ __forceinline__ void split4(const float v[4], uint2& hi, uint2& lo) {
 template <int F16>
 __global__ void __launch_bounds__(MT, 1) k_mr(const __grid_constant__ LaunchParams P,
                                               const __grid_constant__ CUtensorMap rows) {
-    // per-sample data of the current tile
-    __shared__ double sTh[MS], sPh[MS], sPx[MS], sPy[MS], sPz[MS];
-    __shared__ float4 sA[MS];  // cos(b/2), sin(b/2), cos psi0, sin psi0   (b = phi0 - phi_c)
-    __shared__ float4 sB[MS];  // cos theta0, sin theta0, Z_theta, Z_phi
-    __shared__ float2 sBl[MS]; // FP32 remainders of cos(b/2), sin(b/2)
-    __shared__ float sBf[MS];  // b
-    __shared__ int sValid[MS];
-    __shared__ double sPhiC;
-    __shared__ int sRlo, sRhi, sStop, sNb, sNblocks, sPrecise;
-    __shared__ unsigned sBmax, sS0;  // max |sin(b/2)|, max sin(theta0) (float bits)
-    // chunk of MRC rings: union ranges (producers), tables (scheduler)
-    __shared__ float sLo[MRC], sHi[MRC];
-    __shared__ int sFlag[MRC];
+    // per-sample data of two tiles: the planner fills one while the producers use the other
+    __shared__ float4 tA[2][MS];  // cos(b/2), sin(b/2), cos psi0, sin psi0   (b = phi0 - phi_c)
+    __shared__ float4 tB[2][MS];  // cos theta0, sin theta0, Z_theta, Z_phi
+    __shared__ float4 tC[2][MS];  // theta0 as FP32 value + remainder; FP32 remainders of cos(b/2), sin(b/2)
+    __shared__ double tP[2][3][MS];  // unit vector p0 (the FP64 decision in the band)
+    __shared__ int tValid[2][MS];
+    __shared__ TileMeta tMeta[2];
+    // the planner's own per-tile and per-chunk data
+    __shared__ double pPh[MS];  // longitude of the sample in [0, 2 pi)
+    __shared__ float2 pBs[MS];  // b, 1 / (2 sin theta0)
+    __shared__ float sRedF[2][4];
+    __shared__ int sRedI[2], sPlanOk, sNb, sNblocks, sPrecise;
+    __shared__ float sULo[MRC], sUHi[MRC];
+    __shared__ int sUFull[MRC];
     __shared__ int sJref[MRC], sFirst[MRC];
     __shared__ float sArefF[MRC], sDphF[MRC], sSr2[MRC], sInv[MRC];
     __shared__ double sArefD[MRC], sDphD[MRC], sThR[MRC];
     __shared__ int sEntJw[2 * MRC], sEntJ[2 * MRC], sEntLen[2 * MRC], sEntPref[2 * MRC + 1];
-    // pixel table of a window of WINB batches (filled by the producers, one pixel per thread)
-    __shared__ __align__(16) float wSa[NPT];
-    __shared__ __align__(16) float wCa[NPT];
-    __shared__ __align__(16) float wSal[NPT];
-    __shared__ __align__(16) float wCal[NPT];
-    __shared__ int wJw[NPT];
-    __shared__ int wNv[NPT / 8], wPix0[NPT / 8], wRing[NPT / 8];
-    __shared__ float wThh[NPT / 8], wThl[NPT / 8], wSr2[NPT / 8], wInv[NPT / 8];
+    // two windows of WINB batches: per pixel and per block of 8 pixels
+    __shared__ __align__(16) float wSa[2][WPIX];
+    __shared__ __align__(16) float wCa[2][WPIX];
+    __shared__ __align__(16) float wSal[2][WPIX];
+    __shared__ __align__(16) float wCal[2][WPIX];
+    __shared__ int wJw[2][WPIX];
+    __shared__ int wNv[2][WBLK], wPix0[2][WBLK], wRing[2][WBLK];
+    __shared__ float wThh[2][WBLK], wThl[2][WBLK], wSr2[2][WBLK], wInv[2][WBLK];
+    __shared__ WinMeta wMeta[2];
     // stages
     __shared__ int sCtrl[NST];
     __shared__ __align__(8) unsigned long long bLoad[NST], bFull[NST], bEmpty[NST];
+    __shared__ __align__(8) unsigned long long bWinFull[2], bWinEmpty[2], bTileFree[2];
     __shared__ __align__(8) unsigned long long bAccFull, bAccEmpty, bFin, bStall;
     __shared__ unsigned tmem_base;
     __shared__ volatile int failed;
@@ -314,6 +351,11 @@ __global__ void __launch_bounds__(MT, 1) k_mr(const __grid_constant__ LaunchPara
             mbar_init(bLoad + s, 1);
             mbar_init(bFull + s, NPW);
             mbar_init(bEmpty + s, 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(bWinFull + b, 1);
+            mbar_init(bWinEmpty + b, NPW + 1);
+            mbar_init(bTileFree + b, NPW);
         }
         mbar_init(&bAccFull, 1);
         mbar_init(&bAccEmpty, NPW);
@@ -373,50 +415,109 @@ __global__ void __launch_bounds__(MT, 1) k_mr(const __grid_constant__ LaunchPara
             }
         }
         __syncwarp();
-    } else {
-        // ------------------------------------------------------------------ scheduler and producers
-        const bool sched = warp == 1;
-        const int pt = tid - 64;                   // producer thread index (producers only)
-        const int pw = pt >> 5;                    // producer warp 0 .. 15
-        // producer: its sample and pixel quad (block my_q >> 1); a warp takes 32 consecutive
-        // samples of one quad, whose pairs mostly fall inside (or outside) the disc together
-        const int my_t = 32 * (pw & 3) + lane;
-        const int my_q = pw >> 2;
-        const int nc = P.grid_n - 1;
-        const float gmax = (float)(P.grid_n - 2);
+    } else if (warp == 1) {
+        // ------------------------------------------------------------------ scheduler
+        // per batch of the published windows: the stage's control word and the TMA loads of
+        // its two blocks of realization rows
+        unsigned w = 0, it = 0;
+        bool ok = true;
+        while (ok) {
+            const int wb = (int)(w & 1u);
+            ok = warp_wait(bWinFull + wb, (w >> 1) & 1u, &failed, limit, P.err);
+            if (!ok) break;
+            const WinMeta m = wMeta[wb];
+            if (m.flags & W_END) break;
+            for (int fb = 0; fb < m.nb; ++fb) {
+                const int s = (int)(it % NST);
+                const unsigned u = it / NST;
+                if (u > 0 && !warp_wait(bEmpty + s, (u - 1) & 1u, &failed, limit, P.err)) {
+                    ok = false;
+                    break;
+                }
+                const int nv0 = wNv[wb][2 * fb], nv1 = wNv[wb][2 * fb + 1];
+                if (lane == 0) {
+                    sCtrl[s] = ((m.flags & W_TFIRST) && fb == 0 ? CT_FIRST : 0) |
+                               ((m.flags & W_TLAST) && fb == m.nb - 1 ? CT_LAST : 0);
+                    mbar_expect_tx(bLoad + s, (unsigned)(((nv0 > 0) + (nv1 > 0)) * bbytes));
+                }
+                __syncwarp();
+                if (lane < 2 && (lane == 0 ? nv0 : nv1) > 0)
+                    tma_tile4(dyn + s * sbytes + 2 * A_BYTES + lane * bbytes, &rows, wPix0[wb][2 * fb + lane],
+                              bLoad + s);
+                ++it;
+            }
+            if (!ok) break;
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bWinEmpty + wb);
+            ++w;
+        }
+        if (!warp_failed(&failed)) {
+            // the end marker
+            const int s = (int)(it % NST);
+            const unsigned u = it / NST;
+            if (u == 0 || warp_wait(bEmpty + s, (u - 1) & 1u, &failed, limit, P.err)) {
+                if (lane == 0) {
+                    sCtrl[s] = CT_END;
+                    mbar_expect_tx(bLoad + s, 0u);
+                }
+            }
+        }
+        if (failed && lane == 0) {
+            // leave no TMA load in flight: wait (bounded) for the last load of every stage
+            for (int s = 0; s < NST; ++s)
+                if (it > (unsigned)s) mbar_drain(bLoad + s, ((it - 1 - s) / NST) & 1u, limit);
+        }
+        __syncwarp();
+    } else if (warp < NRW) {
+        // ------------------------------------------------------------------ planner (warps 2 and 3)
+        // per tile the samples' constants, per chunk of MRC rings the union of the discs and its
+        // blocks, per window the pixel table; it runs up to two windows (and one tile) ahead.
+        // Its two warps split the samples and the pixels and meet at a named barrier; warp 2
+        // takes every wait and every decision and shares it through shared memory.
+        const int pl = tid - 64, pq = warp - 2;  // planner thread 0 .. 63, planner warp
         const double wr = P.mr_wr;  // 1 - cos R
-        // FP32 membership band of this kernel: pairs with 1 - k . p0 within 2e-5 (relative) of
-        // 1 - cos R take the FP64 decision (a few 1e-5 of the pairs)
         const float wr_hi = P.mr_wr_hi;
-        unsigned it = 0;                           // stage uses (scheduler and producers count alike)
-        int tile_k = 0;                            // tiles processed (accumulator barrier parity)
-
-        for (long long tile = blockIdx.x; tile < P.total_tiles; tile += gridDim.x) {
+        unsigned w = 0;             // windows published
+        int tk = 0;                 // tiles planned
+        bool ok = true;
+        for (long long tile = blockIdx.x; tile < P.total_tiles; tile += gridDim.x, ++tk) {
+            const int tb = tk & 1;
+            // the producers have finished the tile two back (its epilogue reads tValid and tMeta)
+            if (pq == 0) {
+                bool okt = !warp_failed(&failed);
+                if (okt && tk >= 2) okt = warp_wait(bTileFree + tb, (unsigned)(((tk - 2) >> 1) & 1), &failed, limit, P.err);
+                if (lane == 0) sPlanOk = okt ? 1 : 0;
+            }
+            plan_sync();
+            if (!sPlanOk) {
+                ok = false;
+                break;
+            }
             int d = 0;
             while (d + 1 < P.ndet && P.det[d + 1].tile_begin <= tile) ++d;
             const DetEntry& det = P.det[d];
             const long long lt = tile - det.tile_begin;
             const long long t0 = det.begin + lt * MS;
             const int ns = (int)min((long long)MS, det.count - lt * MS);
-            const float* __restrict__ cells = (const float*)det.beam;
 
-            // every producer has finished the previous tile's epilogue (its reads of sValid)
-            // before the per-sample data are rewritten
-            named_sync();
-            // 1. per-sample constants (FP64 basis, FP32 copies)
-            if (!sched && pt < MS) {
-                const int i = pt;
-                bool ok = i < ns;
+            // 1. per-sample constants (FP64 basis, FP32 copies); the colatitude range (rounded
+            //    outwards to FP32), the largest sin theta0 and the first valid sample
+            float tmin = __int_as_float(0x7f800000), tmax = 0.f, s0 = 0.f;
+            int first = MS;
+#pragma unroll 1
+            for (int i = pl; i < MS; i += 64) {
+                bool v = i < ns;
                 double th = 0.0, ph = 0.0, ps = 0.0;
-                if (ok) {
+                if (v) {
                     th = P.theta[t0 + i];
                     ph = P.phi[t0 + i];
                     ps = P.psi[t0 + i];
-                    ok = isfinite(th) && isfinite(ph) && isfinite(ps) && th >= 0.0 && th <= kPi;
+                    v = isfinite(th) && isfinite(ph) && isfinite(ps) && th >= 0.0 && th <= kPi;
                 }
-                float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = make_float4(0.f, 0.f, 0.f, 0.f);
+                float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a, c = a;
                 double px = 0.0, py = 0.0, pz = 0.0, phw = 0.0;
-                if (ok) {
+                float inv2s = 0.f;
+                if (v) {
                     phw = ph - kTwoPi * floor(ph / kTwoPi);
                     if (phw >= kTwoPi) phw -= kTwoPi;
                     double st, ct, sp, cp, ss, cs;
@@ -429,157 +530,162 @@ __global__ void __launch_bounds__(MT, 1) k_mr(const __grid_constant__ LaunchPara
                     a.z = (float)cs;
                     a.w = (float)ss;
                     b = make_float4((float)ct, (float)st, (float)(-cs * st), (float)(ss * st));
+                    c.x = (float)th;
+                    c.y = (float)(th - (double)c.x);
+                    inv2s = 0.5f / b.y;  // +inf at the poles: the whole ring is then taken
+                    tmin = fminf(tmin, __double2float_rd(th));
+                    tmax = fmaxf(tmax, __double2float_ru(th));
+                    s0 = fmaxf(s0, b.y);
+                    first = min(first, i);
                 }
-                sTh[i] = th;
-                sPh[i] = phw;
-                sPx[i] = px;
-                sPy[i] = py;
-                sPz[i] = pz;
-                sA[i] = a;
-                sB[i] = b;
-                sValid[i] = ok ? 1 : 0;
+                tA[tb][i] = a;
+                tB[tb][i] = b;
+                tC[tb][i] = c;
+                tP[tb][0][i] = px;
+                tP[tb][1][i] = py;
+                tP[tb][2][i] = pz;
+                tValid[tb][i] = v ? 1 : 0;
+                pPh[i] = phw;
+                pBs[i] = make_float2(0.f, inv2s);
             }
-            named_sync();
-            if (pt == 0) {
-                int first = -1;
-                double tmin = 1e9, tmax = -1e9, s0 = 0.0;
-                for (int i = 0; i < MS; ++i)
-                    if (sValid[i]) {
-                        if (first < 0) first = i;
-                        tmin = fmin(tmin, sTh[i]);
-                        tmax = fmax(tmax, sTh[i]);
-                        s0 = fmax(s0, (double)sB[i].y);
-                    }
-                sPhiC = first >= 0 ? sPh[first] : 0.0;
-                int ra = 0, rb = -1;
-                if (first >= 0) ring_range(tmin, tmax, P.radius, P.nside, &ra, &rb);
-                sRlo = ra;
-                sRhi = rb;
-                sS0 = __float_as_uint((float)s0);
-                sBmax = 0u;
-                sStop = failed;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                tmin = fminf(tmin, __shfl_xor_sync(0xffffffffu, tmin, o));
+                tmax = fmaxf(tmax, __shfl_xor_sync(0xffffffffu, tmax, o));
+                s0 = fmaxf(s0, __shfl_xor_sync(0xffffffffu, s0, o));
+                first = min(first, __shfl_xor_sync(0xffffffffu, first, o));
             }
-            named_sync();
-            if (sStop) break;
-            if (!sched && pt < MS && sValid[pt]) {
-                double db = sPh[pt] - sPhiC;
-                db -= kTwoPi * rint(db / kTwoPi);
-                double sb, cb;
-                sincos(0.5 * db, &sb, &cb);
-                const float cbf = (float)cb, sbf = (float)sb;
-                sA[pt].x = cbf;
-                sA[pt].y = sbf;
-                sBl[pt] = make_float2((float)(cb - (double)cbf), (float)(sb - (double)sbf));
-                sBf[pt] = (float)db;
-                atomicMax(&sBmax, __float_as_uint(fabsf(sbf)));
+            if (lane == 0) {
+                sRedF[pq][0] = tmin;
+                sRedF[pq][1] = tmax;
+                sRedF[pq][2] = s0;
+                sRedI[pq] = first;
             }
-            named_sync();
+            plan_sync();
+            tmin = fminf(sRedF[0][0], sRedF[1][0]);
+            tmax = fmaxf(sRedF[0][1], sRedF[1][1]);
+            s0 = fmaxf(sRedF[0][2], sRedF[1][2]);
+            first = min(sRedI[0], sRedI[1]);
+            const double phic = first < MS ? pPh[first] : 0.0;
+            int rlo = 0, rhi = -1;
+            if (first < MS) ring_range((double)tmin, (double)tmax, P.radius, P.nside, &rlo, &rhi);
+            //    the longitude offsets b from the tile's reference, as half-angle sines and cosines
+            float bmax = 0.f;
+#pragma unroll 1
+            for (int i = pl; i < MS; i += 64) {
+                if (tValid[tb][i]) {
+                    double db = pPh[i] - phic;
+                    db -= kTwoPi * rint(db / kTwoPi);
+                    double sb, cb;
+                    sincos(0.5 * db, &sb, &cb);
+                    const float cbf = (float)cb, sbf = (float)sb;
+                    tA[tb][i].x = cbf;
+                    tA[tb][i].y = sbf;
+                    tC[tb][i].z = (float)(cb - (double)cbf);
+                    tC[tb][i].w = (float)(sb - (double)sbf);
+                    pBs[i].x = (float)db;
+                    bmax = fmaxf(bmax, fabsf(sbf));
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) bmax = fmaxf(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
+            if (lane == 0) sRedF[pq][3] = bmax;
+            if (pl == 0) {
+                TileMeta tm;
+                tm.t0 = t0;
+                tm.ns = ns;
+                tm.d = d;
+                tMeta[tb] = tm;
+            }
+            plan_sync();
+            bmax = fmaxf(sRedF[0][3], sRedF[1][3]);
 
-            // producer: its sample's constants for the whole tile
-            float4 A4 = make_float4(0.f, 0.f, 0.f, 0.f), B4 = A4;
-            float2 Bl = make_float2(0.f, 0.f);
-            float th0h = 0.f, th0l = 0.f;  // the sample's colatitude as FP32 value + remainder
-            bool tvalid = false;
-            if (!sched) {
-                tvalid = sValid[my_t] != 0;
-                A4 = sA[my_t];
-                B4 = sB[my_t];
-                Bl = sBl[my_t];
-                th0h = (float)sTh[my_t];
-                th0l = (float)(sTh[my_t] - (double)th0h);
-            }
-            int pa_ring = -1;
-            float2 pa = make_float2(0.f, 1e30f);
-            bool tile_first = true;
-
-            const int rlo = sRlo, rhi = sRhi;
+            bool any_window = false;
             const int nch = rhi >= rlo ? (rhi - rlo) / MRC + 1 : 1;
-            for (int ch = 0; ch < nch; ++ch) {
+            for (int ch = 0; ok && ch < nch; ++ch) {
                 const int c0 = rlo + ch * MRC;
                 const int nr = rhi >= rlo ? min(MRC, rhi - c0 + 1) : 0;
                 const bool last_chunk = ch == nch - 1;
-                // 2. per (ring, sample): union of the discs' longitude ranges (producer (ring pt / 16,
-                //    samples pt % 16 + 16 j))
-                if (!sched) {
-                    const int ri = pt >> 4, sub = pt & 15;
-                    float lo = __int_as_float(0x7f800000), hi = -__int_as_float(0x7f800000);
-                    int full = 0;
-                    const bool ring_ok = ri < nr;
-                    const RingInfo* R = ring_ok ? &P.rings[c0 + ri] : nullptr;
-#pragma unroll 4
-                    for (int j = 0; j < MS / 16; ++j) {
-                        const int i = sub + 16 * j;
-                        if (ring_ok && sValid[i]) {
-                            const float h = (float)(0.5 * (R->theta - sTh[i]));
-                            float sh, chh;
-                            sincosf(h, &sh, &chh);
-                            const float av = 2.f * sh * sh;
-                            if (av <= wr_hi) {
-                                const float b2 = 2.f * sB[i].y * R->s_f;
-                                const float tau = (wr_hi - av) / b2;
-                                if (!(b2 > 0.f) || !(tau < 0.999f)) {
-                                    full = 1;
-                                } else {
-                                    const float hw = 2.f * asinf(sqrtf(fmaxf(tau, 0.f)));
-                                    lo = fminf(lo, sBf[i] - hw);
-                                    hi = fmaxf(hi, sBf[i] + hw);
-                                }
+                // 2. ring c0 + lane: the union of the discs' longitude ranges (relative to phi_c)
+                //    over this warp's half of the samples
+                float lo = __int_as_float(0x7f800000), hi = -__int_as_float(0x7f800000);
+                int full = 0;
+                const RingInfo* R = lane < nr ? &P.rings[c0 + lane] : nullptr;
+                if (R) {
+                    const double thr = R->theta;
+                    const float thh = (float)thr, thl = (float)(thr - (double)thh);
+                    const float inv_sr = 1.f / R->s_f;
+#pragma unroll 2
+                    for (int i = 64 * pq; i < 64 * pq + 64; ++i) {
+                        if (!tValid[tb][i]) continue;
+                        const float4 c = tC[tb][i];
+                        // half the colatitude difference: the FP32 values of nearby colatitudes
+                        // subtract exactly, the remainders restore the rest
+                        const float h = 0.5f * ((thh - c.x) + (thl - c.y));
+                        const float sh = sinf(h);
+                        const float av = 2.f * sh * sh;
+                        if (av <= wr_hi) {
+                            // sin^2 of half the longitude half-width: (wr - av) / (2 sin theta0 sin theta_r)
+                            const float2 bs = pBs[i];
+                            const float tau = (wr_hi - av) * bs.y * inv_sr;
+                            if (!(tau < 0.999f)) {
+                                full = 1;
+                            } else {
+                                const float hw = 2.f * asinf(sqrtf(fmaxf(tau, 0.f)));
+                                lo = fminf(lo, bs.x - hw);
+                                hi = fmaxf(hi, bs.x + hw);
                             }
                         }
                     }
-#pragma unroll
-                    for (int off = 8; off > 0; off >>= 1) {
-                        lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, off, 16));
-                        hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, off, 16));
-                        full |= __shfl_xor_sync(0xffffffffu, full, off, 16);
-                    }
-                    if (sub == 0) {
-                        sLo[ri] = lo;
-                        sHi[ri] = hi;
-                        sFlag[ri] = ring_ok ? (full ? 2 : (lo <= hi ? 1 : 0)) : 0;
-                    }
                 }
-                named_sync();
-                // 3. scheduler: per ring the index range of the union, split where it wraps past
-                //    longitude 0, in blocks of 8; the precision bound of the chunk
-                if (sched) {
-                    int cnt = 0, jlo = 0, jref = 0, first = 0, rc = 1;
+                if (pq == 1) {
+                    sULo[lane] = lo;
+                    sUHi[lane] = hi;
+                    sUFull[lane] = full;
+                }
+                plan_sync();
+                if (pq == 0) {
+                    lo = fminf(lo, sULo[lane]);
+                    hi = fmaxf(hi, sUHi[lane]);
+                    full |= sUFull[lane];
+                    // flag 2 = the whole ring, 1 = the range [lo, hi], 0 = no pixel
+                    const int flag = R ? (full ? 2 : (lo <= hi ? 1 : 0)) : 0;
+                    // 3. per ring the index range of the union, split where it wraps past
+                    //    longitude 0, in blocks of 8; the precision bound of the chunk
+                    int cnt = 0, jlo = 0, jref = 0, firstpix = 0, rc = 1;
                     double arefd = 0.0, dphd = 0.0, thr = 0.0;
                     float sr2 = 0.f, inv = 0.f, amax = 0.f, srmax = 0.f;
-                    if (lane < nr) {
-                        const RingInfo& R = P.rings[c0 + lane];
-                        const int flag = sFlag[lane];
-                        first = (int)R.first;
-                        rc = R.count;
-                        sr2 = 2.f * R.s_f;
-                        inv = R.inv_s2_f;
-                        dphd = R.dphi;
-                        thr = R.theta;
-                        const double phic = sPhiC;
-                        jref = (int)rint((phic - R.phi0) / R.dphi);
-                        arefd = R.phi0 + (double)jref * R.dphi - phic;
+                    if (R) {
+                        firstpix = (int)R->first;
+                        rc = R->count;
+                        sr2 = 2.f * R->s_f;
+                        inv = R->inv_s2_f;
+                        dphd = R->dphi;
+                        thr = R->theta;
+                        jref = (int)rint((phic - R->phi0) / R->dphi);
+                        arefd = R->phi0 + (double)jref * R->dphi - phic;
                         if (flag == 2) {
-                            cnt = R.count;
-                            jlo = jref - R.count / 2;
+                            cnt = R->count;
+                            jlo = jref - R->count / 2;
                             amax = 1.f;
                         } else if (flag == 1) {
-                            const double ulo = (phic + (double)sLo[lane] - R.phi0) / R.dphi;
-                            const double uhi = (phic + (double)sHi[lane] - R.phi0) / R.dphi;
+                            const double ulo = (phic + (double)lo - R->phi0) / R->dphi;
+                            const double uhi = (phic + (double)hi - R->phi0) / R->dphi;
                             const long long a = (long long)floor(ulo) - 1, b = (long long)ceil(uhi) + 1;
-                            if (b - a + 1 >= R.count) {
-                                cnt = R.count;
-                                jlo = jref - R.count / 2;
+                            if (b - a + 1 >= R->count) {
+                                cnt = R->count;
+                                jlo = jref - R->count / 2;
                                 amax = 1.f;
                             } else {
                                 cnt = (int)(b - a + 1);
                                 jlo = (int)a;
                                 // largest half-angle of the run's pixels (one pixel of margin each side)
-                                const float ea = fabsf((float)(((double)a - jref) * R.dphi + arefd));
-                                const float eb = fabsf((float)(((double)b - jref) * R.dphi + arefd));
+                                const float ea = fabsf((float)(((double)a - jref) * R->dphi + arefd));
+                                const float eb = fabsf((float)(((double)b - jref) * R->dphi + arefd));
                                 amax = fminf(1.f, fabsf(sinf(0.5f * fminf(fmaxf(ea, eb), 3.1415927f))) + 1e-3f);
                             }
                         }
-                        if (flag != 0) srmax = R.s_f;
+                        if (flag != 0) srmax = R->s_f;
                     }
                     int w0 = 0, l1 = 0, l2 = 0;
                     if (cnt > 0) {
@@ -590,7 +696,7 @@ __global__ void __launch_bounds__(MT, 1) k_mr(const __grid_constant__ LaunchPara
                     }
                     const int b0 = (l1 + 7) >> 3, b1 = (l2 + 7) >> 3;
                     sJref[lane] = jref;
-                    sFirst[lane] = first;
+                    sFirst[lane] = firstpix;
                     sArefF[lane] = (float)arefd;
                     sArefD[lane] = arefd;
                     sDphF[lane] = (float)dphd;
@@ -629,22 +735,32 @@ __global__ void __launch_bounds__(MT, 1) k_mr(const __grid_constant__ LaunchPara
                         // samples, k0 = 2 sin theta0 sin theta_r):
                         //   beta <= 14 u + 2 u sqrt(k0 / wr) (6.2 A + 4 B + 3.2 A B)
                         // with u the FP32 unit roundoff; the fast path needs beta <= the band
-                        const double s0 = __uint_as_float(sS0), bmax = __uint_as_float(sBmax), am = amax;
-                        const double beta = 14.0 * kEps32 + 2.0 * kEps32 * sqrt(2.0 * s0 * srmax / wr) *
-                                                                (6.2 * am + 4.0 * bmax + 3.2 * am * bmax);
+                        const double am = amax, bm = bmax;
+                        const double beta = 14.0 * kEps32 + 2.0 * kEps32 * sqrt(2.0 * (double)s0 * (double)srmax / wr) *
+                                                                (6.2 * am + 4.0 * bm + 3.2 * am * bm);
                         sPrecise = beta > kBand ? 1 : 0;
                     }
                 }
-                named_sync();
+                plan_sync();
                 const int nb = sNb, nblocks = sNblocks, precise = sPrecise;
 
-                // the chunk's batches, in windows of WINB batches (2 WINB blocks, one pixel per
-                // producer thread): the producers first fill the window's pixel table together
+                // the chunk's batches, in windows of WINB batches (2 WINB blocks)
                 for (int wb0 = 0; wb0 < nb; wb0 += WINB) {
                     const int wnb = min(WINB, nb - wb0);
-                    if (!sched) {
-                        // 4. pixel pt of the window: block g = 2 wb0 + pt / 8, pixel pt % 8 of the block
-                        const int g = 2 * wb0 + (pt >> 3), pp = pt & 7;
+                    const int wb = (int)(w & 1u);
+                    if (pq == 0) {
+                        const bool okw = w < 2 || warp_wait(bWinEmpty + wb, ((w >> 1) - 1) & 1u, &failed, limit, P.err);
+                        if (lane == 0) sPlanOk = okw ? 1 : 0;
+                    }
+                    plan_sync();
+                    if (!sPlanOk) {
+                        ok = false;
+                        break;
+                    }
+                    // 4. pixel q of the window: block g = 2 wb0 + q / 8, pixel q % 8 of the block
+#pragma unroll 1
+                    for (int q = pl; q < WPIX; q += 64) {
+                        const int g = 2 * wb0 + (q >> 3), pp = q & 7;
                         float sa = 0.f, ca = 1.f, sal = 0.f, cal = 0.f;
                         int jw = 0;
                         if (g < nblocks) {
@@ -655,8 +771,8 @@ __global__ void __launch_bounds__(MT, 1) k_mr(const __grid_constant__ LaunchPara
                                 else hi_ = mid - 1;
                             }
                             const int e = lo_, ri = e >> 1;
-                            const int bb = g - sEntPref[e];
-                            const int off = 8 * bb + pp;
+                            const int bk = g - sEntPref[e];
+                            const int off = 8 * bk + pp;
                             jw = sEntJw[e] + off;
                             const int j = sEntJ[e] + off;
                             if (precise) {
@@ -672,226 +788,251 @@ __global__ void __launch_bounds__(MT, 1) k_mr(const __grid_constant__ LaunchPara
                                 sincosf(0.5f * aa, &sa, &ca);
                             }
                             if (pp == 0) {
-                                const int wbk = pt >> 3;
-                                wNv[wbk] = min(8, sEntLen[e] - 8 * bb);
-                                wPix0[wbk] = sFirst[ri] + sEntJw[e] + 8 * bb;
-                                wRing[wbk] = c0 + ri;
+                                const int wbk = q >> 3;
+                                wNv[wb][wbk] = min(8, sEntLen[e] - 8 * bk);
+                                wPix0[wb][wbk] = sFirst[ri] + sEntJw[e] + 8 * bk;
+                                wRing[wb][wbk] = c0 + ri;
                                 const float th_h = (float)sThR[ri];
-                                wThh[wbk] = th_h;
-                                wThl[wbk] = (float)(sThR[ri] - (double)th_h);
-                                wSr2[wbk] = sSr2[ri];
-                                wInv[wbk] = sInv[ri];
+                                wThh[wb][wbk] = th_h;
+                                wThl[wb][wbk] = (float)(sThR[ri] - (double)th_h);
+                                wSr2[wb][wbk] = sSr2[ri];
+                                wInv[wb][wbk] = sInv[ri];
                             }
                         } else if (pp == 0) {
-                            wNv[pt >> 3] = 0;
+                            wNv[wb][q >> 3] = 0;
                         }
-                        wSa[pt] = sa;
-                        wCa[pt] = ca;
-                        wSal[pt] = sal;
-                        wCal[pt] = cal;
-                        wJw[pt] = jw;
+                        wSa[wb][q] = sa;
+                        wCa[wb][q] = ca;
+                        wSal[wb][q] = sal;
+                        wCal[wb][q] = cal;
+                        wJw[wb][q] = jw;
                     }
-                    named_sync();
-
-                if (sched) {
-                    // 5. scheduler: the stages of the window's batches (control word, TMA loads)
-                    for (int fb = wb0; fb < wb0 + wnb; ++fb, ++it) {
-                        const int s = (int)(it % NST);
-                        const unsigned u = it / NST;
-                        bool ok = true;
-                        if (lane == 0 && u > 0) ok = mbar_wait(bEmpty + s, (unsigned)((u - 1) & 1), &failed, limit, P.err);
-                        ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0 && !failed;
-                        if (!ok) continue;
-                        const int wbk0 = 2 * (fb - wb0);
-                        const int nv0 = wNv[wbk0], nv1 = wNv[wbk0 + 1];
-                        if (lane == 0) {
-                            sCtrl[s] = (tile_first && fb == 0 ? CT_FIRST : 0) | (last_chunk && fb == nb - 1 ? CT_LAST : 0);
-                            mbar_expect_tx(bLoad + s, (unsigned)(((nv0 > 0) + (nv1 > 0)) * bbytes));
-                        }
-                        __syncwarp();
-                        if (lane < 2 && (lane == 0 ? nv0 : nv1) > 0)
-                            tma_tile4(dyn + s * sbytes + 2 * A_BYTES + lane * bbytes, &rows, wPix0[wbk0 + lane], bLoad + s);
+                    plan_sync();  // the window's entries are written
+                    if (pl == 0) {
+                        WinMeta m;
+                        m.nb = wnb;
+                        m.precise = precise;
+                        m.flags = (any_window ? 0 : W_TFIRST) | (last_chunk && wb0 + wnb == nb ? W_TLAST : 0);
+                        m.tb = tb;
+                        wMeta[wb] = m;
+                        mbar_arrive(bWinFull + wb);
                     }
-                } else {
-                    // 6. producers: weights of (sample my_t, pixels 4 my_q .. 4 my_q + 3) per batch
-                    const int b = my_q >> 1, half = 4 * (my_q & 1);
-                    for (int fb = wb0; fb < wb0 + wnb; ++fb, ++it) {
-                        const int s = (int)(it % NST);
-                        const unsigned u = it / NST;
-                        bool ok = true;
-                        if (u > 0) ok = mbar_wait(bEmpty + s, (unsigned)((u - 1) & 1), &failed, limit, P.err);
-                        if (!__all_sync(0xffffffffu, ok)) continue;
-                        const int wbk = 2 * (fb - wb0) + b;  // the thread's block in the window
-                        const int px0 = 8 * wbk + half;       // its first pixel in the window
-                        const int nv = wNv[wbk];
-                        float w[3][4];
-#pragma unroll
-                        for (int m = 0; m < 3; ++m)
-#pragma unroll
-                            for (int i = 0; i < 4; ++i) w[m][i] = 0.f;
-                        if (tvalid && nv > half) {
-                            const int rg = wRing[wbk];
-                            if (rg != pa_ring) {
-                                // half the colatitude difference: the FP32 values of nearby rings
-                                // subtract exactly, the remainders restore the rest
-                                const float h = 0.5f * ((wThh[wbk] - th0h) + (wThl[wbk] - th0l));
-                                float shh, chh;
-                                sincosf(h, &shh, &chh);
-                                pa = make_float2(2.f * shh * chh, 2.f * shh * shh);
-                                pa_ring = rg;
-                            }
-                            const float sr2 = wSr2[wbk], inv = wInv[wbk];
-                            const float4 sa4 = *(const float4*)&wSa[px0];
-                            const float4 ca4 = *(const float4*)&wCa[px0];
-                            const float sav[4] = {sa4.x, sa4.y, sa4.z, sa4.w};
-                            const float cav[4] = {ca4.x, ca4.y, ca4.z, ca4.w};
-                            const bool prec = precise != 0;
-                            float4 salv4 = make_float4(0.f, 0.f, 0.f, 0.f), calv4 = salv4;
-                            if (prec) {
-                                salv4 = *(const float4*)&wSal[px0];
-                                calv4 = *(const float4*)&wCal[px0];
-                            }
-                            const float salv[4] = {salv4.x, salv4.y, salv4.z, salv4.w};
-                            const float calv[4] = {calv4.x, calv4.y, calv4.z, calv4.w};
-                            const float k0 = B4.y * sr2, k1 = -B4.x * sr2;
-                            const float wlo = P.mr_wr_lo, whi = P.mr_wr_hi;
-                            unsigned band = 0u;  // pairs within the FP32 band of the disc boundary
-#pragma unroll
-                            for (int i = 0; i < 4; ++i) {
-                                if (half + i >= nv) continue;
-                                float sh;
-                                if (prec) {
-                                    // sin((a - b)/2) with the products' rounding errors kept
-                                    const float p1 = sav[i] * A4.x, p2 = cav[i] * A4.y;
-                                    const float e1 = fmaf(sav[i], A4.x, -p1), e2 = fmaf(cav[i], A4.y, -p2);
-                                    const float tl = fmaf(salv[i], A4.x, sav[i] * Bl.x) - fmaf(calv[i], A4.y, cav[i] * Bl.y);
-                                    sh = (p1 - p2) + (tl + (e1 - e2));
-                                } else {
-                                    sh = fmaf(sav[i], A4.x, -cav[i] * A4.y);
-                                }
-                                const float chv = fmaf(cav[i], A4.x, sav[i] * A4.y);
-                                const float sh2 = sh * sh;
-                                const float wv = fmaf(k0, sh2, pa.y);  // 1 - k . p0
-                                if (wv > whi) continue;
-                                if (wv > wlo) band |= 1u << i;  // settled in FP64 below
-                                const float x0 = fmaf(k1, sh2, pa.x);
-                                const float y0 = sr2 * sh * chv;
-                                const float x = fmaf(A4.z, x0, A4.w * y0);   // k . theta'0
-                                const float y = fmaf(A4.z, y0, -A4.w * x0);  // k . phi'0
-                                const float flu = fminf(fmaxf(floorf(fmaf(x, P.invh_f, P.cg_f)), 0.f), gmax);
-                                const float flv = fminf(fmaxf(floorf(fmaf(y, P.invh_f, P.cg_f)), 0.f), gmax);
-                                const float fx = fmaf(x, P.invh_f, P.cg_f - flu);
-                                const float fy = fmaf(y, P.invh_f, P.cg_f - flv);
-                                float4 ka, kb, kc;
-                                ld_cell(cells + 16 * ((int)flv * nc + (int)flu), ka, kb, kc);
-                                const float bA = fmaf(fy, fmaf(fx, ka.w, ka.z), fmaf(fx, ka.y, ka.x));
-                                const float bBq = fmaf(fy, fmaf(fx, kb.w, kb.z), fmaf(fx, kb.y, kb.x));
-                                const float bC = fmaf(fy, fmaf(fx, kc.w, kc.z), fmaf(fx, kc.y, kc.x));
-                                const float qr = rcp_approx(2.f - wv);  // 1 / (1 + k . p0)
-                                const float mp = fmaf(qr, fmaf(x, B4.z, y * B4.w), B4.x);
-                                const float e1 = fmaf(-x, mp, B4.z);
-                                const float e2 = fmaf(-y, mp, B4.w);
-                                const float re = fmaf(e1, e1, -e2 * e2);
-                                const float im2 = e1 * e2;
-                                w[0][i] = bA;
-                                w[1][i] = fmaf(bBq, re, 2.f * bC * im2) * inv;
-                                w[2][i] = fmaf(bC, re, -2.f * bBq * im2) * inv;
-                            }
-                            // pairs in the band take the FP64 decision shared with the other paths
-                            if (band) {
-#pragma unroll
-                                for (int i = 0; i < 4; ++i)
-                                    if (((band >> i) & 1u) &&
-                                        !exact_in_disc(P.rings, rg, wJw[px0 + i], sPx[my_t], sPy[my_t], sPz[my_t],
-                                                       P.cos_r))
-                                        w[0][i] = w[1][i] = w[2][i] = 0.f;
-                            }
-                        }
-                        // the A operand rows: map m, part hi / lo, 8 bytes at core matrix
-                        // (my_t / 8, 2 m + b), row my_t % 8, bytes 8 (my_q % 2) ..
-                        unsigned char* st = dyn + s * sbytes;
-                        const int off = (my_t >> 3) * A_SBO + b * A_LBO + (my_t & 7) * 16 + (my_q & 1) * 8;
-#pragma unroll
-                        for (int m = 0; m < 3; ++m) {
-                            uint2 hi, lo;
-                            split4<F16>(w[m], hi, lo);
-                            *(uint2*)(st + off + m * 2 * A_LBO) = hi;
-                            *(uint2*)(st + A_BYTES + off + m * 2 * A_LBO) = lo;
-                        }
-                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                        __syncwarp();
-                        if (lane == 0) mbar_arrive(bFull + s);
-                    }
-                }
-                named_sync();  // the window's table is rewritten next
-                }
-                tile_first = tile_first && nb == 0;
-                named_sync();  // the chunk's tables are rewritten next
-            }
-
-            // 6. producers: the epilogue, D read back from TMEM (warp w reads lanes 32 (w % 4) ..)
-            if (!sched) {
-                bool ok = true;
-                if (lane == 0) ok = mbar_wait(&bAccFull, (unsigned)(tile_k & 1), &failed, limit, P.err);
-                ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
-                if (ok) {
-                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const int quad = warp & 3, t = 32 * quad + lane;
-                    const int part = nreal / 4;
-                    const int cbeg = ((warp - 2) >> 2) * part;
-                    float* out = (float*)P.out;
-                    const float scale_f = (float)det.scale;
-                    const bool row = t < ns;
-                    const bool vrow = row && sValid[t];
-                    for (int c = cbeg; c < cbeg + part; c += 8) {
-                        unsigned r[8], rl[8];
-                        const unsigned addr = tmem + ((unsigned)(32 * quad) << 16) + (unsigned)c;
-                        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
-                                       "=r"(r[6]), "=r"(r[7])
-                                     : "r"(addr));
-                        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                                     : "=r"(rl[0]), "=r"(rl[1]), "=r"(rl[2]), "=r"(rl[3]), "=r"(rl[4]), "=r"(rl[5]),
-                                       "=r"(rl[6]), "=r"(rl[7])
-                                     : "r"(addr + ncols));
-                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                        if (row) {
-                            float v[8];
-#pragma unroll
-                            for (int j = 0; j < 8; ++j)
-                                v[j] = vrow ? scale_f * (__uint_as_float(r[j]) + __uint_as_float(rl[j]))
-                                            : __int_as_float(0x7fc00000);
-                            float4* o = (float4*)(out + (t0 + t) * nreal + c);
-                            o[0] = make_float4(v[0], v[1], v[2], v[3]);
-                            o[1] = make_float4(v[4], v[5], v[6], v[7]);
-                        }
-                    }
-                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&bAccEmpty);
+                    any_window = true;
+                    ++w;
                 }
             }
-            ++tile_k;
+            if (!ok) break;
         }
-
-        if (sched) {
-            if (!failed) {
-                // the end marker
+        if (ok && pq == 0 && !warp_failed(&failed)) {
+            // the end marker
+            const int wb = (int)(w & 1u);
+            if (w < 2 || warp_wait(bWinEmpty + wb, ((w >> 1) - 1) & 1u, &failed, limit, P.err)) {
+                if (lane == 0) {
+                    wMeta[wb].flags = W_END;
+                    mbar_arrive(bWinFull + wb);
+                }
+            }
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------------------------------------------ weight producers
+        const int pt = tid - 32 * NRW;             // producer thread index
+        const int pw = pt >> 5;                    // producer warp 0 .. 15
+        // its sample and pixel quad (block my_q >> 1); a warp takes 32 consecutive samples of one
+        // quad, whose pairs mostly fall inside (or outside) the disc together
+        const int my_t = 32 * (pw & 3) + lane;
+        const int my_q = pw >> 2;
+        const int b = my_q >> 1, half = 4 * (my_q & 1);
+        const int nc = P.grid_n - 1;
+        const float gmax = (float)(P.grid_n - 2);
+        const float wlo = P.mr_wr_lo, whi = P.mr_wr_hi;
+        unsigned w = 0, it = 0;
+        int tile_k = 0;                            // tiles finished (accumulator barrier parity)
+        // the sample's constants for the current tile
+        float4 A4 = make_float4(0.f, 0.f, 0.f, 0.f), B4 = A4;
+        float2 Bl = make_float2(0.f, 0.f);
+        float th0h = 0.f, th0l = 0.f;              // the sample's colatitude as FP32 value + remainder
+        bool tvalid = false;
+        int pa_ring = -1;
+        float2 pa = make_float2(0.f, 1e30f);
+        const float* __restrict__ cells = nullptr;
+        bool ok = true;
+        while (ok) {
+            const int wb = (int)(w & 1u);
+            ok = warp_wait(bWinFull + wb, (w >> 1) & 1u, &failed, limit, P.err);
+            if (!ok) break;
+            const WinMeta m = wMeta[wb];
+            if (m.flags & W_END) break;
+            const int tb = m.tb;
+            if (m.flags & W_TFIRST) {
+                tvalid = tValid[tb][my_t] != 0;
+                A4 = tA[tb][my_t];
+                B4 = tB[tb][my_t];
+                const float4 c = tC[tb][my_t];
+                th0h = c.x;
+                th0l = c.y;
+                Bl = make_float2(c.z, c.w);
+                pa_ring = -1;
+                cells = (const float*)P.det[tMeta[tb].d].beam;
+            }
+            const bool prec = m.precise != 0;
+            for (int fb = 0; fb < m.nb; ++fb) {
                 const int s = (int)(it % NST);
                 const unsigned u = it / NST;
-                bool ok = true;
-                if (lane == 0 && u > 0) ok = mbar_wait(bEmpty + s, (unsigned)((u - 1) & 1), &failed, limit, P.err);
-                if (lane == 0 && ok) {
-                    sCtrl[s] = CT_END;
-                    mbar_expect_tx(bLoad + s, 0u);
+                bool okw = true;
+                if (u > 0) okw = mbar_wait(bEmpty + s, (u - 1) & 1u, &failed, limit, P.err);
+                if (!__all_sync(0xffffffffu, okw)) {
+                    ok = false;
+                    break;
                 }
+                const int wbk = 2 * fb + b;  // the thread's block in the window
+                const int px0 = 8 * wbk + half;  // its first pixel in the window
+                const int nv = wNv[wb][wbk];
+                float wt[3][4];
+#pragma unroll
+                for (int mm = 0; mm < 3; ++mm)
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) wt[mm][i] = 0.f;
+                if (tvalid && nv > half) {
+                    const int rg = wRing[wb][wbk];
+                    if (rg != pa_ring) {
+                        // half the colatitude difference: the FP32 values of nearby rings
+                        // subtract exactly, the remainders restore the rest
+                        const float h = 0.5f * ((wThh[wb][wbk] - th0h) + (wThl[wb][wbk] - th0l));
+                        float shh, chh;
+                        sincosf(h, &shh, &chh);
+                        pa = make_float2(2.f * shh * chh, 2.f * shh * shh);
+                        pa_ring = rg;
+                    }
+                    const float sr2 = wSr2[wb][wbk], inv = wInv[wb][wbk];
+                    const float4 sa4 = *(const float4*)&wSa[wb][px0];
+                    const float4 ca4 = *(const float4*)&wCa[wb][px0];
+                    const float sav[4] = {sa4.x, sa4.y, sa4.z, sa4.w};
+                    const float cav[4] = {ca4.x, ca4.y, ca4.z, ca4.w};
+                    float4 salv4 = make_float4(0.f, 0.f, 0.f, 0.f), calv4 = salv4;
+                    if (prec) {
+                        salv4 = *(const float4*)&wSal[wb][px0];
+                        calv4 = *(const float4*)&wCal[wb][px0];
+                    }
+                    const float salv[4] = {salv4.x, salv4.y, salv4.z, salv4.w};
+                    const float calv[4] = {calv4.x, calv4.y, calv4.z, calv4.w};
+                    const float k0 = B4.y * sr2, k1 = -B4.x * sr2;
+                    unsigned band = 0u;  // pairs within the FP32 band of the disc boundary
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        if (half + i >= nv) continue;
+                        float sh;
+                        if (prec) {
+                            // sin((a - b)/2) with the products' rounding errors kept
+                            const float p1 = sav[i] * A4.x, p2 = cav[i] * A4.y;
+                            const float e1 = fmaf(sav[i], A4.x, -p1), e2 = fmaf(cav[i], A4.y, -p2);
+                            const float tl = fmaf(salv[i], A4.x, sav[i] * Bl.x) - fmaf(calv[i], A4.y, cav[i] * Bl.y);
+                            sh = (p1 - p2) + (tl + (e1 - e2));
+                        } else {
+                            sh = fmaf(sav[i], A4.x, -cav[i] * A4.y);
+                        }
+                        const float chv = fmaf(cav[i], A4.x, sav[i] * A4.y);
+                        const float sh2 = sh * sh;
+                        const float wv = fmaf(k0, sh2, pa.y);  // 1 - k . p0
+                        if (wv > whi) continue;
+                        if (wv > wlo) band |= 1u << i;  // settled in FP64 below
+                        const float x0 = fmaf(k1, sh2, pa.x);
+                        const float y0 = sr2 * sh * chv;
+                        const float x = fmaf(A4.z, x0, A4.w * y0);   // k . theta'0
+                        const float y = fmaf(A4.z, y0, -A4.w * x0);  // k . phi'0
+                        const float flu = fminf(fmaxf(floorf(fmaf(x, P.invh_f, P.cg_f)), 0.f), gmax);
+                        const float flv = fminf(fmaxf(floorf(fmaf(y, P.invh_f, P.cg_f)), 0.f), gmax);
+                        const float fx = fmaf(x, P.invh_f, P.cg_f - flu);
+                        const float fy = fmaf(y, P.invh_f, P.cg_f - flv);
+                        float4 ka, kb, kc;
+                        ld_cell(cells + 16 * ((int)flv * nc + (int)flu), ka, kb, kc);
+                        const float bA = fmaf(fy, fmaf(fx, ka.w, ka.z), fmaf(fx, ka.y, ka.x));
+                        const float bBq = fmaf(fy, fmaf(fx, kb.w, kb.z), fmaf(fx, kb.y, kb.x));
+                        const float bC = fmaf(fy, fmaf(fx, kc.w, kc.z), fmaf(fx, kc.y, kc.x));
+                        const float qr = rcp_approx(2.f - wv);  // 1 / (1 + k . p0)
+                        const float mp = fmaf(qr, fmaf(x, B4.z, y * B4.w), B4.x);
+                        const float e1 = fmaf(-x, mp, B4.z);
+                        const float e2 = fmaf(-y, mp, B4.w);
+                        const float re = fmaf(e1, e1, -e2 * e2);
+                        const float im2 = e1 * e2;
+                        wt[0][i] = bA;
+                        wt[1][i] = fmaf(bBq, re, 2.f * bC * im2) * inv;
+                        wt[2][i] = fmaf(bC, re, -2.f * bBq * im2) * inv;
+                    }
+                    // pairs in the band take the FP64 decision shared with the other paths
+                    if (band) {
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+                            if (((band >> i) & 1u) &&
+                                !exact_in_disc(P.rings, rg, wJw[wb][px0 + i], tP[tb][0][my_t], tP[tb][1][my_t],
+                                               tP[tb][2][my_t], P.cos_r))
+                                wt[0][i] = wt[1][i] = wt[2][i] = 0.f;
+                    }
+                }
+                // the A operand rows: map m, part hi / lo, 8 bytes at core matrix
+                // (my_t / 8, 2 m + b), row my_t % 8, bytes 8 (my_q % 2) ..
+                unsigned char* st = dyn + s * sbytes;
+                const int off = (my_t >> 3) * A_SBO + b * A_LBO + (my_t & 7) * 16 + (my_q & 1) * 8;
+#pragma unroll
+                for (int mm = 0; mm < 3; ++mm) {
+                    uint2 hi, lo;
+                    split4<F16>(wt[mm], hi, lo);
+                    *(uint2*)(st + off + mm * 2 * A_LBO) = hi;
+                    *(uint2*)(st + A_BYTES + off + mm * 2 * A_LBO) = lo;
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 __syncwarp();
-            } else if (lane == 0) {
-                // leave no TMA load in flight: wait (bounded) for the last load of every stage
-                for (int s = 0; s < NST; ++s)
-                    if (it > (unsigned)s) mbar_drain(bLoad + s, ((it - 1 - s) / NST) & 1u, limit);
+                if (lane == 0) mbar_arrive(bFull + s);
+                ++it;
             }
+            if (!ok) break;
             __syncwarp();
+            if (lane == 0) mbar_arrive(bWinEmpty + wb);
+            if (m.flags & W_TLAST) {
+                // the epilogue, D read back from TMEM (warp w reads lanes 32 (w % 4) ..)
+                ok = warp_wait(&bAccFull, (unsigned)(tile_k & 1), &failed, limit, P.err);
+                if (!ok) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const TileMeta tm = tMeta[tb];
+                const int quad = warp & 3, t = 32 * quad + lane;
+                const int part = nreal / 4;
+                const int cbeg = ((warp - NRW) >> 2) * part;
+                float* out = (float*)P.out;
+                const float scale_f = (float)P.det[tm.d].scale;
+                const bool row = t < tm.ns;
+                const bool vrow = row && tValid[tb][t];
+                for (int c = cbeg; c < cbeg + part; c += 8) {
+                    unsigned r[8], rl[8];
+                    const unsigned addr = tmem + ((unsigned)(32 * quad) << 16) + (unsigned)c;
+                    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                                   "=r"(r[6]), "=r"(r[7])
+                                 : "r"(addr));
+                    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                                 : "=r"(rl[0]), "=r"(rl[1]), "=r"(rl[2]), "=r"(rl[3]), "=r"(rl[4]), "=r"(rl[5]),
+                                   "=r"(rl[6]), "=r"(rl[7])
+                                 : "r"(addr + ncols));
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    if (row) {
+                        float v[8];
+#pragma unroll
+                        for (int j = 0; j < 8; ++j)
+                            v[j] = vrow ? scale_f * (__uint_as_float(r[j]) + __uint_as_float(rl[j]))
+                                        : __int_as_float(0x7fc00000);
+                        float4* o = (float4*)(out + (tm.t0 + t) * nreal + c);
+                        o[0] = make_float4(v[0], v[1], v[2], v[3]);
+                        o[1] = make_float4(v[4], v[5], v[6], v[7]);
+                    }
+                }
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) {
+                    mbar_arrive(&bAccEmpty);
+                    mbar_arrive(bTileFree + tb);
+                }
+                ++tile_k;
+            }
+            ++w;
         }
     }
 
