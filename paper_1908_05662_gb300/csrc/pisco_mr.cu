@@ -839,10 +839,10 @@ __global__ void __launch_bounds__(MT, 1) k_mr(const __grid_constant__ LaunchPara
         const int pt = tid - 32 * NRW;             // producer thread index
         const int pw = pt >> 5;                    // producer warp 0 .. 15
         // its sample and pixel quad (block my_q >> 1); a warp takes 32 consecutive samples of one
-        // quad, whose pairs mostly fall inside (or outside) the disc together
+        // quad, whose pairs mostly fall inside (or outside) the disc together.  The quad turns
+        // with the batch, so the quads that end a block (more often empty) fall to every warp
         const int my_t = 32 * (pw & 3) + lane;
-        const int my_q = pw >> 2;
-        const int b = my_q >> 1, half = 4 * (my_q & 1);
+        const int q0 = pw >> 2;
         const int nc = P.grid_n - 1;
         const float gmax = (float)(P.grid_n - 2);
         const float wlo = P.mr_wr_lo, whi = P.mr_wr_hi;
@@ -885,6 +885,8 @@ __global__ void __launch_bounds__(MT, 1) k_mr(const __grid_constant__ LaunchPara
                     ok = false;
                     break;
                 }
+                const int my_q = (q0 + (int)it) & 3;
+                const int b = my_q >> 1, half = 4 * (my_q & 1);
                 const int wbk = 2 * fb + b;  // the thread's block in the window
                 const int px0 = 8 * wbk + half;  // its first pixel in the window
                 const int nv = wNv[wb][wbk];
@@ -893,7 +895,7 @@ __global__ void __launch_bounds__(MT, 1) k_mr(const __grid_constant__ LaunchPara
                 for (int mm = 0; mm < 3; ++mm)
 #pragma unroll
                     for (int i = 0; i < 4; ++i) wt[mm][i] = 0.f;
-                if (tvalid && nv > half) {
+                if (nv > half) {  // warp-uniform: the quad has pixels
                     const int rg = wRing[wb][wbk];
                     if (rg != pa_ring) {
                         // half the colatitude difference: the FP32 values of nearby rings
@@ -918,46 +920,64 @@ __global__ void __launch_bounds__(MT, 1) k_mr(const __grid_constant__ LaunchPara
                     const float calv[4] = {calv4.x, calv4.y, calv4.z, calv4.w};
                     const float k0 = B4.y * sr2, k1 = -B4.x * sr2;
                     unsigned band = 0u;  // pairs within the FP32 band of the disc boundary
+                    // two pairs at a time: both pairs' geometry, then both beam cells in flight
+                    // together, then both pairs' weights (a pair no lane has inside skips its load
+                    // and weights; lanes outside a pair's disc compute it and keep zero)
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        if (half + i >= nv) continue;
-                        float sh;
-                        if (prec) {
-                            // sin((a - b)/2) with the products' rounding errors kept
-                            const float p1 = sav[i] * A4.x, p2 = cav[i] * A4.y;
-                            const float e1 = fmaf(sav[i], A4.x, -p1), e2 = fmaf(cav[i], A4.y, -p2);
-                            const float tl = fmaf(salv[i], A4.x, sav[i] * Bl.x) - fmaf(calv[i], A4.y, cav[i] * Bl.y);
-                            sh = (p1 - p2) + (tl + (e1 - e2));
-                        } else {
-                            sh = fmaf(sav[i], A4.x, -cav[i] * A4.y);
+                    for (int hp = 0; hp < 4; hp += 2) {
+                        float wv[2], x[2], y[2], fx[2], fy[2];
+                        const float* cp[2];
+                        bool in[2];
+#pragma unroll
+                        for (int j = 0; j < 2; ++j) {
+                            const int i = hp + j;
+                            float sh;
+                            if (prec) {
+                                // sin((a - b)/2) with the products' rounding errors kept
+                                const float p1 = sav[i] * A4.x, p2 = cav[i] * A4.y;
+                                const float e1 = fmaf(sav[i], A4.x, -p1), e2 = fmaf(cav[i], A4.y, -p2);
+                                const float tl = fmaf(salv[i], A4.x, sav[i] * Bl.x) - fmaf(calv[i], A4.y, cav[i] * Bl.y);
+                                sh = (p1 - p2) + (tl + (e1 - e2));
+                            } else {
+                                sh = fmaf(sav[i], A4.x, -cav[i] * A4.y);
+                            }
+                            const float chv = fmaf(cav[i], A4.x, sav[i] * A4.y);
+                            const float sh2 = sh * sh;
+                            wv[j] = fmaf(k0, sh2, pa.y);  // 1 - k . p0
+                            in[j] = tvalid && half + i < nv && wv[j] <= whi;
+                            if (in[j] && wv[j] > wlo) band |= 1u << i;  // settled in FP64 below
+                            const float x0 = fmaf(k1, sh2, pa.x);
+                            const float y0 = sr2 * sh * chv;
+                            x[j] = fmaf(A4.z, x0, A4.w * y0);   // k . theta'0
+                            y[j] = fmaf(A4.z, y0, -A4.w * x0);  // k . phi'0
+                            // clamped to the grid, so every lane's cell address is valid
+                            const float flu = fminf(fmaxf(floorf(fmaf(x[j], P.invh_f, P.cg_f)), 0.f), gmax);
+                            const float flv = fminf(fmaxf(floorf(fmaf(y[j], P.invh_f, P.cg_f)), 0.f), gmax);
+                            fx[j] = fmaf(x[j], P.invh_f, P.cg_f - flu);
+                            fy[j] = fmaf(y[j], P.invh_f, P.cg_f - flv);
+                            cp[j] = cells + 16 * ((int)flv * nc + (int)flu);
                         }
-                        const float chv = fmaf(cav[i], A4.x, sav[i] * A4.y);
-                        const float sh2 = sh * sh;
-                        const float wv = fmaf(k0, sh2, pa.y);  // 1 - k . p0
-                        if (wv > whi) continue;
-                        if (wv > wlo) band |= 1u << i;  // settled in FP64 below
-                        const float x0 = fmaf(k1, sh2, pa.x);
-                        const float y0 = sr2 * sh * chv;
-                        const float x = fmaf(A4.z, x0, A4.w * y0);   // k . theta'0
-                        const float y = fmaf(A4.z, y0, -A4.w * x0);  // k . phi'0
-                        const float flu = fminf(fmaxf(floorf(fmaf(x, P.invh_f, P.cg_f)), 0.f), gmax);
-                        const float flv = fminf(fmaxf(floorf(fmaf(y, P.invh_f, P.cg_f)), 0.f), gmax);
-                        const float fx = fmaf(x, P.invh_f, P.cg_f - flu);
-                        const float fy = fmaf(y, P.invh_f, P.cg_f - flv);
-                        float4 ka, kb, kc;
-                        ld_cell(cells + 16 * ((int)flv * nc + (int)flu), ka, kb, kc);
-                        const float bA = fmaf(fy, fmaf(fx, ka.w, ka.z), fmaf(fx, ka.y, ka.x));
-                        const float bBq = fmaf(fy, fmaf(fx, kb.w, kb.z), fmaf(fx, kb.y, kb.x));
-                        const float bC = fmaf(fy, fmaf(fx, kc.w, kc.z), fmaf(fx, kc.y, kc.x));
-                        const float qr = rcp_approx(2.f - wv);  // 1 / (1 + k . p0)
-                        const float mp = fmaf(qr, fmaf(x, B4.z, y * B4.w), B4.x);
-                        const float e1 = fmaf(-x, mp, B4.z);
-                        const float e2 = fmaf(-y, mp, B4.w);
-                        const float re = fmaf(e1, e1, -e2 * e2);
-                        const float im2 = e1 * e2;
-                        wt[0][i] = bA;
-                        wt[1][i] = fmaf(bBq, re, 2.f * bC * im2) * inv;
-                        wt[2][i] = fmaf(bC, re, -2.f * bBq * im2) * inv;
+                        const bool any0 = __any_sync(0xffffffffu, in[0]), any1 = __any_sync(0xffffffffu, in[1]);
+                        float4 ka[2], kb[2], kc[2];
+                        if (any0) ld_cell(cp[0], ka[0], kb[0], kc[0]);
+                        if (any1) ld_cell(cp[1], ka[1], kb[1], kc[1]);
+#pragma unroll
+                        for (int j = 0; j < 2; ++j) {
+                            if (!(j == 0 ? any0 : any1)) continue;
+                            const int i = hp + j;
+                            const float bA = fmaf(fy[j], fmaf(fx[j], ka[j].w, ka[j].z), fmaf(fx[j], ka[j].y, ka[j].x));
+                            const float bBq = fmaf(fy[j], fmaf(fx[j], kb[j].w, kb[j].z), fmaf(fx[j], kb[j].y, kb[j].x));
+                            const float bC = fmaf(fy[j], fmaf(fx[j], kc[j].w, kc[j].z), fmaf(fx[j], kc[j].y, kc[j].x));
+                            const float qr = rcp_approx(2.f - wv[j]);  // 1 / (1 + k . p0)
+                            const float mp = fmaf(qr, fmaf(x[j], B4.z, y[j] * B4.w), B4.x);
+                            const float e1 = fmaf(-x[j], mp, B4.z);
+                            const float e2 = fmaf(-y[j], mp, B4.w);
+                            const float re = fmaf(e1, e1, -e2 * e2);
+                            const float im2 = e1 * e2;
+                            wt[0][i] = in[j] ? bA : 0.f;
+                            wt[1][i] = in[j] ? fmaf(bBq, re, 2.f * bC * im2) * inv : 0.f;
+                            wt[2][i] = in[j] ? fmaf(bC, re, -2.f * bBq * im2) * inv : 0.f;
+                        }
                     }
                     // pairs in the band take the FP64 decision shared with the other paths
                     if (band) {
