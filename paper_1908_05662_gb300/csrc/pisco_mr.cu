@@ -135,6 +135,18 @@ __device__ __forceinline__ bool mbar_try(unsigned addr, unsigned parity) {
     return done != 0;
 }
 
+// The same test, letting the thread sleep until the phase completes or about a microsecond
+// passes, so that waiting warps leave the issue slots to the others.
+__device__ __forceinline__ bool mbar_try_sleep(unsigned addr, unsigned parity) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(addr), "r"(parity), "r"(1000u)
+        : "memory");
+    return done != 0;
+}
+
 // Wait for the phase of the given parity.  Gives up when the block's failure
 // flag is raised, or after `limit` SM clocks, when it raises the flag and
 // records error bit 2.
@@ -144,7 +156,7 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
     if (mbar_try(a, parity)) return true;
     const long long t0 = clock64();
     while (true) {
-        if (mbar_try(a, parity)) return true;
+        if (mbar_try_sleep(a, parity)) return true;
         if (*failed) return false;
         if (clock64() - t0 > limit) {
             *failed = 1;
@@ -158,7 +170,7 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
 __device__ __forceinline__ bool mbar_drain(unsigned long long* bar, unsigned parity, long long limit) {
     const unsigned a = smem_u32(bar);
     const long long t0 = clock64();
-    while (!mbar_try(a, parity))
+    while (!mbar_try_sleep(a, parity))
         if (clock64() - t0 > limit) return false;
     return true;
 }
