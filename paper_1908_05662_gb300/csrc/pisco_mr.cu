@@ -100,7 +100,7 @@ constexpr int A_BYTES = MS * KB * 2;      // one 16-bit weight part of a batch (
 constexpr int B_ATOM = 8 * 64;            // one swizzle atom: 8 pixels (K) x 32 realizations (N)
 constexpr int B_LBO = 3 * B_ATOM;         // bytes between atoms adjacent in N
 constexpr unsigned kSwizzle64 = 4u;       // descriptor layout type: 64-byte swizzling
-__host__ __device__ constexpr int block_bytes(int nreal) { return 48 * nreal; }  // K-adjacent core matrices
+__host__ __device__ constexpr int block_bytes(int nreal) { return 48 * nreal; }  // one block: 8 pixels x 3 maps x R
 __host__ __device__ constexpr int stage_bytes(int nreal) { return 2 * A_BYTES + 2 * block_bytes(nreal); }
 enum { CT_FIRST = 1, CT_LAST = 2, CT_END = 4 };            // stage control word
 enum { W_TFIRST = 1, W_TLAST = 2, W_END = 4 };             // window flags: a tile's first / last window
