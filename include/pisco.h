@@ -56,7 +56,7 @@ typedef enum pisco_status {
     PISCO_ECUDA = 3,         /* a CUDA runtime call failed */
     PISCO_ETIMEOUT = 4,      /* a bounded device wait gave up (reported by pisco_sync_status) */
     PISCO_EUNSUPPORTED = 5,  /* valid request this build does not implement */
-    PISCO_EDEVICE = 6        /* a kernel recorded an invariant violation */
+    PISCO_EDEVICE = 6        /* a kernel recorded an invariant violation (reserved) */
 } pisco_status;
 
 /* Arithmetic of a plan (pisco_options.precision).  tile_samples and
@@ -420,9 +420,11 @@ pisco_status pisco_plan_autotune_batched(pisco_plan* plan, int n_det, const int6
 
 /* Synchronise the plan's work on `stream` and report any error a kernel
  * recorded since the last call, clearing it: PISCO_ETIMEOUT when a bounded
- * device wait gave up (flag 2: the multi-realization kernel waits about two
- * seconds at most for its MMAs and its TMA loads, then stops issuing, frees
- * its tensor memory and returns), PISCO_EDEVICE for any other flag. */
+ * device wait gave up (flag 2: every mbarrier wait of the multi-realization
+ * kernel, on its MMAs, its TMA loads and its warps' hand-offs, gives up after
+ * about two seconds, and the kernel then stops issuing, frees its tensor
+ * memory and returns), PISCO_EDEVICE for any other flag (no kernel records
+ * one at present: the value is kept for invariant checks). */
 pisco_status pisco_sync_status(pisco_plan* plan, void* stream);
 
 #ifdef __cplusplus
