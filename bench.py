@@ -77,6 +77,12 @@ HBM_GBS, BF16_TFLOPS, PEAK_SOURCE = measured_peaks()
 #   serving scattered 32-byte sectors of beam cells.
 FORWARD_PROFILE = {(10_000_000, 16, 1): {"traffic": 486.63e6 + 47.03e6, "l1tex_pct": 93.1, "lts_pct": 78.1}}
 
+# Recorded ncu figures of the multi-realization kernel (BF16, 256 realizations) on a 2e5-sample
+# slice of its workload (profiles/k_mr_multirealization.md), not measured by this run: the tensor
+# pipe's busy fraction (it issues the hi and lo weight parts, twice the algorithmic flops) and the
+# warp schedulers' issue rate, which show that the FP32 weight producers, not the tensor cores, bind.
+MR_PROFILE = {"tensor_pipe_pct": 20.1, "issue_per_cycle": 0.57, "l1tex_pct": 65.3}
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -513,7 +519,13 @@ def run_multireal(args, dev):
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": BF16_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / BF16_TFLOPS, "traffic": None, "peak_source": PEAK_SOURCE,
                      "note": "algorithmic 2*3*pairs*R flops (the hi/lo weight split doubles the issued MMAs); "
-                             "dense BF16 burst peak"},
+                             "dense BF16 burst peak",
+                     "binding_unit": "FP32 weight producers (geometry, beam cells, Ludwig-3 rotation per pair)",
+                     "tensor_pipe_pct": MR_PROFILE["tensor_pipe_pct"] if n_real == 256 else None,
+                     "issue_per_cycle": MR_PROFILE["issue_per_cycle"] if n_real == 256 else None,
+                     "l1tex_throughput_pct": MR_PROFILE["l1tex_pct"] if n_real == 256 else None,
+                     "unit_pct_note": "recorded ncu figures of this kernel at 256 realizations "
+                                      "(profiles/k_mr_multirealization.md), not measured by this run"},
         "gpu_launches": args.steps, "clocks": clk}))
 
 
