@@ -7,8 +7,13 @@ and returns with its tensor memory released; the host sees PISCO_ETIMEOUT from
 pisco_sync_status, the flag is cleared, and the next launch on the same plan
 gives the TOD it gave before (the kernel is deterministic), which matches the
 oracle.  No GPU fault is involved.
+
+Host-side fault injection of an allocation failure: a plan whose realization
+stack cannot fit in device memory fails its allocation before anything is read
+from the caller's buffers (PISCO_ENOMEM), and the device serves the next plan.
 """
 
+import ctypes
 import math
 
 import numpy as np
@@ -79,3 +84,39 @@ def test_stall_hook_rejects_other_plans_and_bad_lengths():
             with pytest.raises(pisco.PiscoError) as e:
                 plan.inject_mr_stall(bad)
             assert e.value.status == pisco.PISCO_EINVAL
+
+
+def test_allocation_failure_reports_enomem_and_the_device_serves_the_next_plan():
+    """256 BF16 realizations at nside 7723 ask for a 1.1 TB stack, several times the device
+    memory: the stack's allocation fails before anything is read from `sky` (a small buffer
+    here), so the call returns PISCO_ENOMEM with a message and no plan."""
+    lib = pisco.load_library()
+    nside, n_real = 7723, 256
+    need = 12 * nside * nside * 3 * n_real * 2
+    if need <= 2 * torch.cuda.get_device_properties(0).total_memory:
+        pytest.skip("the device could hold the stack")
+    small = torch.zeros(64, dtype=torch.bfloat16, device=DEV)
+    grids = torch.zeros(1, 6, 11, 11, device=DEV)
+    handle = ctypes.c_void_p()
+    det = (pisco.pisco_detector * 1)(pisco.pisco_detector(0.0, 0.0, 1.0))
+    opt = pisco.pisco_options(pisco.PISCO_BF16_MR, 0, 0, 0, n_real)
+    st = lib.pisco_plan_create(ctypes.byref(handle), nside, 0.1, ctypes.c_void_p(small.data_ptr()),
+                               pisco.PISCO_DTYPE_BF16, 1, det, 11, ctypes.c_void_p(grids.data_ptr()), None,
+                               ctypes.byref(opt), None)
+    assert st == pisco.PISCO_ENOMEM
+    assert handle.value is None
+    assert b"allocation" in lib.pisco_last_error(None)
+    torch.cuda.synchronize()
+
+    # the next plan works and matches the oracle
+    nside, r, n = 16, math.radians(10.0), 40
+    sky = sy.gaussian_sky(nside, 5)
+    g = sy.random_beam_maps(31, 6)
+    det = (0.2, 0.02, 1.0)
+    th, ph, ps = sy.random_pointings(n, 9)
+    ref = oc.tod(nside, r, sky.numpy(), g.astype(np.float64), det, ob.omega_tilde(g[0].astype(np.float64), r),
+                 th, ph, ps)
+    with pisco.Plan(nside, r, sky.to(DEV), [det], torch.as_tensor(g, device=DEV)[None]) as plan:
+        out = plan.convolve(_t(th), _t(ph), _t(ps)).double().cpu().numpy()
+        plan.sync_status()
+    assert np.max(np.abs(out - ref)) <= 2e-6 * np.max(np.abs(ref))
